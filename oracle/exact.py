@@ -1,0 +1,100 @@
+"""Oracle-X: exact state-vector propagation of Eq. 1 for at most 9 atoms.
+
+State psi in C^(3^N) with basis index sum_i s_i 3^i (s_i in {0:|0>, 1:|1>, 2:|r>}),
+so atom 0 is the fastest index.  Time stepping is piecewise constant: step k
+uses H(t_k + dt/2) and psi <- exp(-i H dt) psi, the same time discretisation
+the TDVP step uses (reading A8).  The exponential is NOT a Krylov method:
+
+* N <= 6: dense Hermitian eigendecomposition (numpy.linalg.eigh),
+* N <= 9: scipy.sparse.linalg.expm_multiply (Al-Mohy & Higham truncated Taylor).
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import model
+
+MAX_ATOMS = 9
+
+
+def basis_index(states):
+    """Index of the product basis state with per-atom levels ``states``."""
+    return int(sum(int(s) * 3 ** i for i, s in enumerate(states)))
+
+
+def product_state(amps):
+    """Kronecker product of per-atom 3-vectors (atom 0 fastest)."""
+    amps = np.asarray(amps, dtype=np.complex128)
+    psi = np.ones(1, dtype=np.complex128)
+    for i in range(amps.shape[0]):
+        # atom i has stride 3^i: it is the slower factor of kron(a_i, psi)
+        psi = np.kron(amps[i], psi)
+    return psi
+
+
+def diagonal_interaction(V):
+    """Diagonal of sum_{i<j} V_ij n_i n_j in the product basis."""
+    n = V.shape[0]
+    dim = 3 ** n
+    idx = np.arange(dim)
+    ryd = np.zeros((n, dim), dtype=bool)
+    for i in range(n):
+        ryd[i] = (idx // 3 ** i) % 3 == 2
+    d = np.zeros(dim)
+    for i in range(n):
+        for j in range(i + 1, n):
+            if V[i, j] != 0.0:
+                d += V[i, j] * (ryd[i] & ryd[j])
+    return d
+
+
+def hamiltonian(V, schedule, t):
+    """Sparse H(t) of Eq. 1 on the full 3^N space."""
+    n = V.shape[0]
+    if n > MAX_ATOMS:
+        raise ValueError("exact oracle is limited to %d atoms" % MAX_ATOMS)
+    ox, oz, w, de = model.coefficients(schedule, n, t)
+    H = sp.diags(diagonal_interaction(V).astype(np.complex128), format="csr")
+    for i in range(n):
+        h = model.local_term(ox[i], oz[i], w[i], de[i])
+        if not np.any(h):
+            continue
+        # atom i has stride 3^i: kron(I_{3^(n-1-i)}, h, I_{3^i})
+        op = sp.kron(sp.identity(3 ** (n - 1 - i), format="csr"),
+                     sp.kron(sp.csr_matrix(h), sp.identity(3 ** i, format="csr")),
+                     format="csr")
+        H = H + op
+    return H.tocsr()
+
+
+def step(psi, V, schedule, t, dt):
+    """One piecewise-constant step exp(-i H(t+dt/2) dt) psi."""
+    H = hamiltonian(V, schedule, t + 0.5 * dt)
+    n = V.shape[0]
+    if n <= 6:
+        w, U = np.linalg.eigh(H.toarray())
+        return U @ (np.exp(-1j * dt * w) * (U.conj().T @ psi))
+    return spla.expm_multiply(-1j * dt * H, psi)
+
+
+def evolve(psi, V, schedule, t0, dt, n_steps):
+    t = t0
+    for _ in range(n_steps):
+        psi = step(psi, V, schedule, t, dt)
+        t += dt
+    return psi
+
+
+def expectation_local(psi, n_atoms, op):
+    """<psi| op_i |psi> for every atom i (op a 3x3 matrix)."""
+    T = psi.reshape([3] * n_atoms, order="F")
+    out = np.zeros(n_atoms)
+    for i in range(n_atoms):
+        opT = np.moveaxis(np.tensordot(op, T, axes=([1], [i])), 0, i)
+        out[i] = np.real(np.vdot(T, opT))
+    return out
+
+
+def energy(psi, V, schedule, t):
+    H = hamiltonian(V, schedule, t)
+    return float(np.real(np.vdot(psi, H @ psi)))
