@@ -1,0 +1,177 @@
+/*
+ * ttn.h -- C ABI of libttn: single-GPU (sm_103a) TTN-TDVP for the Rydberg
+ * digital twin of arXiv 2210.03763.
+ *
+ * What it computes.  A binary tree tensor network (TTN) over an Lx x Ly
+ * lattice of three-level atoms (|0>, |1>, |r>), with leaves in Hilbert-curve
+ * order (Sec. "Tensor network simulations"), evolved by the single-site
+ * time-dependent variational principle under the Rydberg Hamiltonian
+ *
+ *   H(t) = sum_i [ Ox_i sx_i + Oz_i sz_i + (W_i |r><1|_i + h.c.) - Delta_i n_i ]
+ *        + sum_{i<j} V_ij n_i n_j ,          V_ij = C6 / d_ij^6        (Eq. 1, Eq. 2)
+ *
+ * with W_i = Omega^R_i exp(i phase_i), sx = |0><1| + |1><0|, sz = |0><0| - |1><1|,
+ * n = |r><r|.  The detuning term -Delta n is the CZ pulse's detuning of
+ * Sec. "Compiler for global GHZ states", which Eq. 1 does not print.  Eq. 2
+ * prints V = -C6/d^6: here C6 is passed with its sign and V_ij = C6/d_ij^6.
+ *
+ * Conventions for every call.
+ *  - Host arrays passed in are owned by the caller and copied before return.
+ *  - The context owns all device memory; nothing is shared between contexts.
+ *  - Work is issued on the context's stream (ttn_set_stream); calls that
+ *    return host scalars synchronise that stream.
+ *  - No call throws.  Each returns a ttn_status; on error the context keeps a
+ *    message (ttn_last_error).  Invalid arguments return TTN_ERR_ARG and leave
+ *    the context unchanged.  Device-side numerical failures (NaN/Inf) are
+ *    reported as TTN_ERR_NUMERIC at the next synchronising call.
+ *  - Complex numbers are interleaved (re, im) doubles.
+ *  - Atom i sits at lattice site (i % Lx, i / Lx).
+ *  - Node numbering: level-0 nodes (pairs of leaves 2j, 2j+1) first, left to
+ *    right, then level 1, ..., the root last.  Node k has legs
+ *    (child 0, child 1, parent) with dims (d0, d1, d2); the root's parent leg
+ *    is a dummy leg of dim 1.  A node tensor X is stored with
+ *    X(a, b, c) at index a + d0*(b + d1*c) (child 0 fastest).
+ *  - Bond dimension of the parent leg of a node whose subtree holds the real
+ *    atom set S: min(chi, 3^|S|, 3^(N - |S|)).  Leaves are padded to a power
+ *    of two; padding leaves hold no atom, stay in |0> and carry no term
+ *    (Sec. "Parallel quantum algorithms").
+ */
+#ifndef TTN_H
+#define TTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttn_ctx ttn_ctx;
+
+typedef enum {
+    TTN_OK = 0,
+    TTN_ERR_ARG = 1,      /* invalid argument; nothing changed                  */
+    TTN_ERR_ALLOC = 2,    /* device or host allocation failed                   */
+    TTN_ERR_CUDA = 3,     /* a CUDA runtime call failed (message has the name)  */
+    TTN_ERR_KRYLOV = 4,   /* Lanczos did not reach its tolerance in m_max steps */
+    TTN_ERR_NUMERIC = 5,  /* NaN or Inf met in the state                        */
+    TTN_ERR_TIMEOUT = 6,  /* a bounded device-side wait gave up                 */
+    TTN_ERR_STATE = 7     /* call not valid in the current state                */
+} ttn_status;
+
+typedef enum {
+    TTN_FP64 = 0,         /* all contractions in FP64 (complex128)              */
+    TTN_SPLIT_TF32X3 = 1  /* H_eff and environment contractions as split-TF32
+                             tensor-core GEMMs (3 products, FP32 accumulate);
+                             Lanczos, tridiagonal exponential and QR stay FP64  */
+} ttn_precision;
+
+/* One piecewise-constant drive segment of one atom, active on [t0, t1).
+ * Active segments of the same atom add up.  Layout: 64 bytes. */
+typedef struct {
+    int32_t atom;
+    double t0, t1;
+    double omega_x;   /* coefficient of sx                       */
+    double omega_z;   /* coefficient of sz                       */
+    double omega_r;   /* Omega^R of Omega^R e^{i phase}|r><1| + h.c. */
+    double phase_r;
+    double delta;     /* coefficient of -n                       */
+} ttn_pulse;
+
+/* Create a context for an Lx x Ly lattice of atoms with `levels` local states
+ * (must be 3) and maximal bond dimension chi >= 1.  The state starts as
+ * |0...0>, the Hamiltonian as H = 0 (unit square positions, C6 = 0), internal
+ * time t = 0, precision TTN_FP64, the stream the legacy default stream.
+ * Lx*Ly must be in [1, 1024].  *out receives the context or NULL. */
+ttn_status ttn_create(int Lx, int Ly, int levels, int chi, ttn_ctx** out);
+void ttn_destroy(ttn_ctx* ctx);
+const char* ttn_last_error(const ttn_ctx* ctx);
+
+/* Issue all later work on this CUDA stream (a cudaStream_t, e.g. PyTorch's
+ * current stream); NULL selects the legacy default stream. */
+ttn_status ttn_set_stream(ttn_ctx* ctx, void* cuda_stream);
+ttn_status ttn_set_precision(ttn_ctx* ctx, ttn_precision p);
+
+/* Positions xy (N x 2 doubles, atom-major), pair coefficient C6 (signed,
+ * V_ij = C6/d_ij^6, Eq. 2) and interaction radius r_cut: pairs farther apart
+ * than r_cut are dropped (the radius r_I = r_G + d_off of Sec. "Tensor network
+ * simulations"); r_cut <= 0 keeps all pairs.  Coincident positions or
+ * non-finite values -> TTN_ERR_ARG.  Rebuilds the environments. */
+ttn_status ttn_set_hamiltonian(ttn_ctx* ctx, const double* xy, double C6, double r_cut);
+
+/* Replace the drive schedule by n_segments segments (copied).  Atoms outside
+ * [0, N) or t1 < t0 -> TTN_ERR_ARG.  Drives are evaluated at the midpoint of
+ * each TDVP step (Sec. "Tensor network simulations": per-layer control). */
+ttn_status ttn_apply_pulse(ttn_ctx* ctx, const ttn_pulse* schedule, int n_segments);
+
+/* Set the state to a product state: amps holds N x 3 complex amplitudes
+ * (interleaved, atom-major, level order |0>,|1>,|r>).  Bond bases are filled
+ * by the deterministic completion rule; the centre is at the root.  Resets
+ * the internal time to 0. */
+ttn_status ttn_set_product_state(ttn_ctx* ctx, const double* amps);
+
+/* Set the state of ctx to (|0..0> + e^{i phase} |m>)/sqrt2 where |m> has the
+ * atoms with mask[i] != 0 in |1> and the others in |0>: the exact bond-
+ * dimension-2 TTN of the GHZ target (Sec. "Tensor network simulations"). */
+ttn_status ttn_set_ghz_target(ttn_ctx* ctx, const int* mask, double phase);
+
+/* One second-order TDVP step of length dt > 0 at H(t + dt/2), advancing the
+ * internal time t by dt.  Sweep: forward half-sweep with dt/2 (children first,
+ * links evolved backwards on the way up) followed by its reverse. */
+ttn_status ttn_tdvp_step(ttn_ctx* ctx, double dt);
+
+/* F = |<target|psi>|^2 (unnormalised, Sec. "Parallel quantum algorithms").
+ * target must have the same lattice; its chi may differ. */
+ttn_status ttn_fidelity(ttn_ctx* ctx, const ttn_ctx* target, double* F);
+/* <target|psi> as a complex number (2 doubles). */
+ttn_status ttn_overlap(ttn_ctx* ctx, const ttn_ctx* target, double* re_im);
+
+/* Per-atom expectation values (N doubles): which = 0 -> <|0><0|>,
+ * 1 -> <|1><1|>, 2 -> <n> = <|r><r|> (P_R of Sec. "Modeling 88Sr quantum
+ * computers" is their sum). */
+ttn_status ttn_measure(ttn_ctx* ctx, int which, double* out);
+ttn_status ttn_norm(ttn_ctx* ctx, double* out);      /* <psi|psi>                 */
+ttn_status ttn_energy(ttn_ctx* ctx, double* out);    /* <psi|H(t)|psi>, current t */
+ttn_status ttn_get_time(ttn_ctx* ctx, double* t);
+
+/* Full state vector (3^N complex, index sum_i s_i 3^i) for N <= 9. */
+ttn_status ttn_get_dense(ttn_ctx* ctx, double* psi);
+
+/* Save / load the tree state (node tensors, time, chi, lattice) to a file.
+ * Load needs a context with the same lattice and chi. */
+ttn_status ttn_save(ttn_ctx* ctx, const char* path);
+ttn_status ttn_load(ttn_ctx* ctx, const char* path);
+
+/* ---- introspection used by tests and tools ------------------------------ */
+ttn_status ttn_num_nodes(const ttn_ctx* ctx, int* n);
+/* dims[3] = (d0, d1, d2); children[2] = child node ids, or -(leaf+1) for a leaf. */
+ttn_status ttn_node_info(const ttn_ctx* ctx, int node, int* dims, int* children);
+/* leaf_atom[n_leaves]: atom id per leaf in Hilbert order, -1 for padding. */
+ttn_status ttn_leaf_atoms(const ttn_ctx* ctx, int* leaf_atom, int* n_leaves);
+/* Copy node tensor to / from host (d0*d1*d2 complex).  ttn_set_node leaves
+ * the environments stale until ttn_refresh_envs; callers that set every node
+ * must keep the canonical form (non-root nodes isometric towards the root). */
+ttn_status ttn_get_node(ttn_ctx* ctx, int node, double* data);
+ttn_status ttn_set_node(ttn_ctx* ctx, int node, const double* data);
+/* Rebuild every upward environment from the current node tensors (centre at
+ * the root).  Needed after ttn_set_node. */
+ttn_status ttn_refresh_envs(ttn_ctx* ctx);
+
+/* Y = H_eff(node) X for the centre at `node`: moves the orthogonality centre
+ * to `node` (gauge moves only, the state is unchanged), then applies the
+ * effective Hamiltonian of the node at H(t) to the host tensor x (same shape
+ * as the node) and writes y.  Used to check the contraction element by
+ * element.  The centre stays at `node` until the next step or observable,
+ * which move it back to the root. */
+ttn_status ttn_apply_heff(ttn_ctx* ctx, int node, const double* x, double* y);
+
+/* Counters since the last ttn_reset_stats: [0] Krylov runs, [1] Krylov
+ * matvecs, [2] max Krylov error estimate (as double bits), [3] kernel launches
+ * issued by the library, [4] QR calls, [5] dependent columns completed. */
+ttn_status ttn_get_stats(const ttn_ctx* ctx, int64_t* out6);
+ttn_status ttn_reset_stats(ttn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTN_H */

@@ -8,7 +8,7 @@
 """
 import numpy as np
 
-QR_RANK_TOL = 1e-13          # |R_kk| <= tol * ||A||_F  -> column treated as dependent
+QR_RANK_TOL = 1e-10          # |R_kk| <= tol * ||A||_F  -> column treated as dependent
 COMPLETION_MIN_RES2 = 0.25   # candidate accepted if its residual norm^2 >= 1/4
 KRYLOV_TOL = 1e-13
 KRYLOV_MMAX = 30
@@ -32,7 +32,7 @@ def qr_complete(A, row_order=None, tol=QR_RANK_TOL):
 
     Column-by-column classical Gram-Schmidt with one re-orthogonalisation
     pass (CGS2).  Column k is *dependent* when its residual after both passes
-    has norm <= tol * ||A||_F; then R_kk = 0 and Q's column k is filled after
+    has norm <= tol * ||A||_F (tol = 1e-10); then R_kk = 0 and Q's column k is filled after
     all columns are processed, in increasing k, by the first candidate unit
     vector e_c (candidates in ``row_order``) with 1 - ||Q^H e_c||^2 >= 1/4
     (else the candidate with the largest such residual, first in order on

@@ -1,0 +1,94 @@
+// Internal declarations shared by the CUDA translation units of libttn.
+// Not part of the ABI (include/ttn.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+typedef double2 cplx;   // (re, im)
+
+// Generic strided complex contraction, the one primitive every tensor
+// contraction of the TDVP update is mapped to:
+//   C[b](m, n) = alpha * sum_k op(A)[b](m, k) * op(B)[b](k, n) + beta * C[b](m, n)
+// with k = ki + Ki*ko and b = bi + Bi*bo, each index with its own stride
+// (in complex elements).  op = identity or complex conjugation.
+struct GemmArgs {
+    int M, N, Ki, Ko, Bi, Bo;
+    const cplx* A; long long a_m, a_ki, a_ko, a_bi, a_bo; int conjA;
+    const cplx* B; long long b_ki, b_ko, b_n, b_bi, b_bo; int conjB;
+    cplx* C; long long c_m, c_n, c_bi, c_bo;
+    cplx alpha, beta;
+};
+
+// Launch on `stream`; returns the number of kernels launched (0 if empty).
+int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream);
+// Split-precision tensor-core path (3xTF32 on tcgen05); falls back to nothing:
+// returns -1 when the shape is not supported so the caller can use FP64.
+int launch_zgemm_split(const GemmArgs& g, cudaStream_t stream, void* workspace,
+                       size_t workspace_bytes);
+size_t split_workspace_bytes(const GemmArgs& g);
+
+// ---- Lanczos / vector kernels (kernels.cu) --------------------------------
+// Fixed partial-sum grid for reductions: deterministic order, no atomics.
+constexpr int RED_BLOCKS = 304;     // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int KRYLOV_MMAX = 30;
+
+struct KrylovScalars {
+    double alpha[KRYLOV_MMAX];
+    double beta[KRYLOV_MMAX + 1];
+    cplx   h[KRYLOV_MMAX + 1];      // projections of the current pass
+    cplx   c[KRYLOV_MMAX];          // exp(z T_j) e_1
+    double nrm0;                    // norm of the start vector
+    double inv_scale;               // 1 / beta_j used to normalise v_{j+1}
+    double err;                     // a-posteriori error estimate
+    int    converged;
+    int    nonfinite;
+};
+
+int k_norm2_partial(const cplx* x, long long n, double* partial, cudaStream_t s);
+int k_dots_partial(const cplx* V, long long ld, int nv, const cplx* w, long long n,
+                   cplx* partial, cudaStream_t s);
+int k_reduce_dots(const cplx* partial, int nv, cplx* out, cudaStream_t s);
+int k_reduce_norm(const double* partial, double* out, cudaStream_t s);
+// w -= sum_i V_i h_i; then (mode 1) partial dots of the new w with V_0..V_{nv-1},
+// or (mode 2) the partial norm^2 of the new w.
+int k_orth_update(const cplx* V, long long ld, int nv, const cplx* h, cplx* w, long long n,
+                  int mode, cplx* partial_dots, double* partial_norm, cudaStream_t s);
+int k_scale_copy(const cplx* x, long long n, const double* scale, int invert_sqrt,
+                 cplx* y, cudaStream_t s);
+int k_combine(const cplx* V, long long ld, int nv, const KrylovScalars* ks, cplx* y,
+              long long n, cudaStream_t s);
+// Krylov step bookkeeping: alpha_j, beta_j, tridiagonal exponential, error.
+int k_krylov_scalars(KrylovScalars* ks, const cplx* h1, const cplx* h2,
+                     const double* beta2, int j, double z_re, double z_im,
+                     double tol, cudaStream_t s);
+int k_krylov_start(KrylovScalars* ks, const double* nrm2, cudaStream_t s);
+
+// ---- elementwise / assembly ---------------------------------------------------
+int k_permute3(const cplx* x, cplx* y, int d0, int d1, int d2, int p0, int p1, int p2,
+               int inverse, cudaStream_t s);
+int k_fill(cplx* x, long long n, cplx v, cudaStream_t s);
+// H = Hs + sum_i coef_i-weighted drive ops (see kernels.cu)
+int k_assemble_block(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsites,
+                     const int* site_ids, const cplx* dops, int ndriven,
+                     const int* driven_ids, const double* coef, cudaStream_t s);
+int k_check_finite(const cplx* x, long long n, int* flag, cudaStream_t s);
+
+// ---- QR (qr.cu) ----------------------------------------------------------------
+struct QrScratch {
+    cplx* part;         // RED_BLOCKS * (D + 1) partial dots
+    cplx* h;            // D + 1 projections
+    double* pnorm;      // RED_BLOCKS partial norms
+    double* scal;       // scalars: [0] ||A||_F^2, [1] current column norm, ...
+    int* flags;         // per-column dependent flags (D)
+    double* rownorm;    // M row norms of Q (completion)
+    int* cand;          // candidate order (M)
+    int* pick;          // chosen candidate
+};
+// In-place QR of the column-major M x D matrix A (lda = M): A <- Q, R (D x D,
+// column-major) written.  cand[0..ncand) is the completion candidate order.
+int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand,
+            QrScratch& ws, cudaStream_t s, int* n_dependent_host);
+
+#define TTN_LAUNCH_CHECK() (cudaGetLastError())

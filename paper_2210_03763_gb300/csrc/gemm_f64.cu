@@ -1,0 +1,126 @@
+// FP64 complex strided contraction (see GemmArgs in common.cuh).
+//
+// Every contraction of the TDVP update -- a matrix on one leg of a 3-leg node
+// tensor, the channel sums of the cross terms, the environment
+// renormalisations X^H (op x X) -- is one call of this kernel with suitable
+// strides.  Tile: 64 x 64 complex outputs per CTA, 256 threads, 4 x 4 complex
+// accumulators per thread, K staged through shared memory in slices of 8.
+// GB300's FP64 pipe (about 2 DFMA/clk/SM) is the bound, not memory: a simple
+// register-tiled loop is enough to saturate it, so loads use generic strides
+// (with bounds checks that zero-fill) rather than TMA.
+#include "common.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 8;
+constexpr int TM = 4, TN = 4;            // per-thread complex tile
+constexpr int THREADS = (BM / TM) * (BN / TN);
+
+__device__ __forceinline__ cplx cmul_acc(cplx acc, cplx a, cplx b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+
+__global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
+    __shared__ cplx As[2][BK][BM];
+    __shared__ cplx Bs[2][BK][BN];
+
+    const int b = blockIdx.z;
+    const int bi = b % g.Bi, bo = b / g.Bi;
+    const cplx* A = g.A + bi * g.a_bi + bo * g.a_bo;
+    const cplx* B = g.B + bi * g.b_bi + bo * g.b_bo;
+    cplx* C = g.C + bi * g.c_bi + bo * g.c_bo;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int K = g.Ki * g.Ko;
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+
+    cplx acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+    // each thread stages 2 elements of the A slice and 2 of the B slice
+    auto load = [&](int k0, int buf) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int e = tid + r * THREADS;            // 0 .. BK*BM-1
+            int kk = e / BM, mm = e % BM;         // A: m fastest
+            int m = m0 + mm, k = k0 + kk;
+            cplx v = make_double2(0.0, 0.0);
+            if (m < g.M && k < K) {
+                int ki = k % g.Ki, ko = k / g.Ki;
+                v = A[m * g.a_m + ki * g.a_ki + ko * g.a_ko];
+                if (g.conjA) v.y = -v.y;
+            }
+            As[buf][kk][mm] = v;
+            int kb = e / BN, nn = e % BN;         // B: n fastest
+            int n = n0 + nn, k2 = k0 + kb;
+            cplx w = make_double2(0.0, 0.0);
+            if (n < g.N && k2 < K) {
+                int ki = k2 % g.Ki, ko = k2 / g.Ki;
+                w = B[ki * g.b_ki + ko * g.b_ko + n * g.b_n];
+                if (g.conjB) w.y = -w.y;
+            }
+            Bs[buf][kb][nn] = w;
+        }
+    };
+
+    int buf = 0;
+    load(0, 0);
+    __syncthreads();
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        if (k0 + BK < K) load(k0 + BK, buf ^ 1);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            cplx a[TM], bb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + i * (BM / TM)];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx + j * (BN / TN)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = cmul_acc(acc[i][j], a[i], bb[j]);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+
+    const bool beta0 = (g.beta.x == 0.0 && g.beta.y == 0.0);
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int m = m0 + ty + i * (BM / TM);
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int n = n0 + tx + j * (BN / TN);
+            if (n >= g.N) continue;
+            cplx* cp = C + m * g.c_m + n * g.c_n;
+            cplx v = acc[i][j];
+            cplx r;
+            r.x = g.alpha.x * v.x - g.alpha.y * v.y;
+            r.y = g.alpha.x * v.y + g.alpha.y * v.x;
+            if (!beta0) {
+                cplx c0 = *cp;
+                r.x += g.beta.x * c0.x - g.beta.y * c0.y;
+                r.y += g.beta.x * c0.y + g.beta.y * c0.x;
+            }
+            *cp = r;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream) {
+    if (g.M <= 0 || g.N <= 0 || g.Bi <= 0 || g.Bo <= 0) return 0;
+    long long batches = (long long)g.Bi * g.Bo;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)batches);
+    zgemm_f64_kernel<<<grid, THREADS, 0, stream>>>(g);
+    return 1;
+}

@@ -1,0 +1,436 @@
+// Vector, reduction and small-matrix kernels of the TDVP update.
+//
+// Reductions never use atomics: each of G blocks writes a partial sum for a
+// contiguous chunk of the vector, and every consumer sums the G partials in
+// the same fixed order, so repeated runs are bitwise identical and every
+// block of a kernel sees the same reduced value.
+#include "common.cuh"
+#include <cmath>
+
+namespace {
+
+constexpr int T = RED_THREADS;
+
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ cplx cdotc(cplx a, cplx b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ void chunk_of(long long n, int G, long long& lo, long long& hi) {
+    long long c = (n + G - 1) / G;
+    lo = (long long)blockIdx.x * c;
+    hi = lo + c < n ? lo + c : n;
+}
+
+// Block-wide sum of one complex value per thread (result valid in thread 0).
+__device__ cplx block_sum_c(cplx v, cplx* sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    cplx r = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = cadd(r, sh[i]);
+    return r;
+}
+
+__device__ double block_sum_d(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    return r;
+}
+
+// Sum the G partials of nv projections (partial[i*G + g]) into sh_h[0..nv).
+__device__ void reduce_partials_to_shared(const cplx* partial, int nv, int G, cplx* sh_h) {
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        cplx s = make_double2(0.0, 0.0);
+        for (int g = 0; g < G; ++g) s = cadd(s, partial[(long long)i * G + g]);
+        sh_h[i] = s;
+    }
+    __syncthreads();
+}
+
+__device__ double reduce_norm_partials(const double* partial, int G) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += partial[g];
+    return s;
+}
+
+// ---------------------------------------------------------------- kernels
+// (optional) column `scale_col` of V *= factor(norm partials); then partial
+// dots conj(V_i) . w for i < nv over this block's chunk.
+__global__ void dots_kernel(cplx* V, long long ld, int nv, const cplx* w, long long n, int G,
+                            cplx* partial, int scale_col, const double* scale_src, int scale_mode,
+                            long long skip_col) {
+    __shared__ cplx sh[T / 32];
+    long long lo, hi;
+    chunk_of(n, G, lo, hi);
+    if (scale_col >= 0) {
+        // scale_mode 1: factor = 1/sqrt(sum partials) or 0 if flagged dependent
+        double f = scale_src[0];
+        cplx* col = V + (long long)scale_col * ld;
+        for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            cplx x = col[e];
+            col[e] = make_double2(x.x * f, x.y * f);
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < nv; ++i) {
+        cplx s = make_double2(0.0, 0.0);
+        if (i != skip_col) {
+            const cplx* vi = V + (long long)i * ld;
+            for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s = cadd(s, cdotc(vi[e], w[e]));
+        }
+        s = block_sum_c(s, sh);
+        if (threadIdx.x == 0) partial[(long long)i * G + blockIdx.x] = s;
+    }
+}
+
+// h = reduce(partial_in); w -= sum_i V_i h_i (i != skip); then mode 1: partial
+// dots of the new w, mode 2: partial norm^2.  Block 0 also stores h to h_out
+// (accumulated into h_out when accumulate != 0).
+__global__ void orth_update_kernel(const cplx* V, long long ld, int nv, const cplx* partial_in,
+                                   cplx* w, long long n, int G, int mode, cplx* partial_dots,
+                                   double* partial_norm, cplx* h_out, int accumulate,
+                                   long long skip_col) {
+    __shared__ cplx sh_h[KRYLOV_MMAX + 260];
+    __shared__ cplx shc[T / 32];
+    __shared__ double shd[T / 32];
+    reduce_partials_to_shared(partial_in, nv, G, sh_h);
+    if (blockIdx.x == 0 && h_out != nullptr) {
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+            cplx v = sh_h[i];
+            if (i == skip_col) v = make_double2(0.0, 0.0);
+            h_out[i] = accumulate ? cadd(h_out[i], v) : v;
+        }
+    }
+    long long lo, hi;
+    chunk_of(n, G, lo, hi);
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        cplx x = w[e];
+        for (int i = 0; i < nv; ++i) {
+            if (i == skip_col) continue;
+            cplx p = cmul(V[(long long)i * ld + e], sh_h[i]);
+            x.x -= p.x;
+            x.y -= p.y;
+        }
+        w[e] = x;
+    }
+    if (mode == 1) {
+        __syncthreads();
+        for (int i = 0; i < nv; ++i) {
+            cplx s = make_double2(0.0, 0.0);
+            if (i != skip_col) {
+                const cplx* vi = V + (long long)i * ld;
+                for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s = cadd(s, cdotc(vi[e], w[e]));
+            }
+            s = block_sum_c(s, shc);
+            if (threadIdx.x == 0) partial_dots[(long long)i * G + blockIdx.x] = s;
+        }
+    } else if (mode == 2) {
+        double s = 0.0;
+        for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s += w[e].x * w[e].x + w[e].y * w[e].y;
+        s = block_sum_d(s, shd);
+        if (threadIdx.x == 0) partial_norm[blockIdx.x] = s;
+    }
+}
+
+__global__ void norm2_partial_kernel(const cplx* x, long long n, int G, double* partial) {
+    __shared__ double shd[T / 32];
+    long long lo, hi;
+    chunk_of(n, G, lo, hi);
+    double s = 0.0;
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s += x[e].x * x[e].x + x[e].y * x[e].y;
+    s = block_sum_d(s, shd);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void scale_copy_kernel(const cplx* x, long long n, const double* scale, cplx* y) {
+    double f = scale[0];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        cplx v = x[e];
+        y[e] = make_double2(v.x * f, v.y * f);
+    }
+}
+
+__global__ void combine_kernel(const cplx* V, long long ld, int nv, const KrylovScalars* ks, cplx* y,
+                               long long n) {
+    __shared__ cplx c[KRYLOV_MMAX];
+    if (threadIdx.x < nv) {
+        cplx ci = ks->c[threadIdx.x];
+        c[threadIdx.x] = make_double2(ci.x * ks->nrm0, ci.y * ks->nrm0);
+    }
+    __syncthreads();
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        cplx s = make_double2(0.0, 0.0);
+        for (int i = 0; i < nv; ++i) s = cadd(s, cmul(V[(long long)i * ld + e], c[i]));
+        y[e] = s;
+    }
+}
+
+// exp(z T) e_1 for the real symmetric tridiagonal T (diag a[0..m), off-diag
+// b[0..m-1)), m <= 32, by the truncated Taylor series of the matrix
+// exponential applied to the vector, with the step z split into n_sub equal
+// substeps so that |z/n_sub| * ||T||_inf <= 1/2 (the "Taylor series" method of
+// Moler & Van Loan, "Nineteen dubious ways to compute the exponential of a
+// matrix", with scaling).  One warp; lane i holds component i.
+__device__ void tridiag_expm_warp(const double* a, const double* b, int m, double zr, double zi,
+                                  cplx* out) {
+    const int l = threadIdx.x & 31;
+    double ai = l < m ? a[l] : 0.0;
+    double bl = (l < m - 1) ? b[l] : 0.0;          // T(l, l+1)
+    double bu = (l >= 1 && l < m) ? b[l - 1] : 0.0; // T(l, l-1)
+    double rs = fabs(ai) + fabs(bl) + fabs(bu);
+    for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, o));
+    double zn = sqrt(zr * zr + zi * zi);
+    int nsub = (int)ceil(zn * rs / 0.5);
+    if (nsub < 1) nsub = 1;
+    double hr = zr / nsub, hi = zi / nsub;
+    cplx u = make_double2(l == 0 ? 1.0 : 0.0, 0.0);
+    for (int s = 0; s < nsub; ++s) {
+        cplx term = u, sum = u;
+        for (int k = 1; k <= 40; ++k) {
+            // t = T term
+            double xm_r = __shfl_up_sync(0xffffffffu, term.x, 1);
+            double xm_i = __shfl_up_sync(0xffffffffu, term.y, 1);
+            double xp_r = __shfl_down_sync(0xffffffffu, term.x, 1);
+            double xp_i = __shfl_down_sync(0xffffffffu, term.y, 1);
+            double tr = ai * term.x + (l >= 1 ? bu * xm_r : 0.0) + (l < 31 ? bl * xp_r : 0.0);
+            double ti = ai * term.y + (l >= 1 ? bu * xm_i : 0.0) + (l < 31 ? bl * xp_i : 0.0);
+            if (l >= m) { tr = 0.0; ti = 0.0; }
+            // term = (h * t) / k
+            double inv = 1.0 / k;
+            term = make_double2((hr * tr - hi * ti) * inv, (hr * ti + hi * tr) * inv);
+            sum = cadd(sum, term);
+            double tm = fabs(term.x) + fabs(term.y);
+            double sm = fabs(sum.x) + fabs(sum.y);
+            for (int o = 16; o > 0; o >>= 1) {
+                tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+                sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+            }
+            if (tm <= 1e-18 * sm) break;
+        }
+        u = sum;
+    }
+    if (l < m) out[l] = u;
+}
+
+__global__ void krylov_start_kernel(KrylovScalars* ks, const double* nrm2_partial, int G) {
+    if (threadIdx.x != 0) return;
+    double s = reduce_norm_partials(nrm2_partial, G);
+    double n0 = sqrt(s);
+    ks->nrm0 = n0;
+    ks->inv_scale = n0 > 0.0 ? 1.0 / n0 : 0.0;
+    ks->converged = (n0 == 0.0) ? 1 : 0;
+    ks->nonfinite = isfinite(n0) ? 0 : 1;
+    ks->err = 0.0;
+    for (int i = 0; i < KRYLOV_MMAX; ++i) ks->c[i] = make_double2(0.0, 0.0);
+}
+
+__global__ void krylov_scalars_kernel(KrylovScalars* ks, const cplx* h1, const cplx* h2,
+                                      const double* beta_partial, int G, int j, double zr,
+                                      double zi, double tol) {
+    __shared__ double a[32], b[32];
+    if (threadIdx.x == 0) {
+        ks->alpha[j] = h1[j].x + h2[j].x;
+        double b2 = reduce_norm_partials(beta_partial, G);
+        ks->beta[j] = sqrt(b2);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int l = threadIdx.x;
+        a[l] = l <= j ? ks->alpha[l] : 0.0;
+        b[l] = l < j ? ks->beta[l] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) tridiag_expm_warp(a, b, j + 1, zr, zi, ks->c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bj = ks->beta[j];
+        cplx cj = ks->c[j];
+        double err = bj * sqrt(cj.x * cj.x + cj.y * cj.y);
+        ks->err = err;
+        ks->converged = (err <= tol) ? 1 : 0;
+        ks->inv_scale = bj > 0.0 ? 1.0 / bj : 0.0;
+        if (!isfinite(err) || !isfinite(ks->alpha[j])) ks->nonfinite = 1;
+    }
+}
+
+__global__ void permute3_kernel(const cplx* x, cplx* y, int d0, int d1, int d2, int p0, int p1, int p2,
+                                int inverse) {
+    // y has axes (x-axis p0, x-axis p1, x-axis p2), first fastest
+    long long n = (long long)d0 * d1 * d2;
+    int dims[3] = {d0, d1, d2};
+    int q[3] = {p0, p1, p2};
+    int e0 = dims[q[0]], e1 = dims[q[1]];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long i0 = e % e0, r = e / e0;
+        long long i1 = r % e1, i2 = r / e1;
+        long long idx[3];
+        idx[q[0]] = i0;
+        idx[q[1]] = i1;
+        idx[q[2]] = i2;
+        long long src = idx[0] + (long long)d0 * (idx[1] + (long long)d1 * idx[2]);
+        if (!inverse) y[e] = x[src];
+        else y[src] = x[e];
+    }
+}
+
+__global__ void fill_kernel(cplx* x, long long n, cplx v) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        x[e] = v;
+}
+
+// coef: 5 doubles per atom (omega_x, omega_z, Re W, Im W, delta)
+__global__ void assemble_block_kernel(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsites,
+                                      const int* site_ids, const cplx* dops, int ndriven,
+                                      const int* driven_ids, const double* coef) {
+    long long DD = (long long)D * D;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < DD;
+         e += (long long)gridDim.x * blockDim.x) {
+        int a = (int)(e % D), b = (int)(e / D);
+        long long et = b + (long long)D * a;           // transposed position
+        cplx h = Hs ? Hs[e] : make_double2(0.0, 0.0);
+        for (int i = 0; i < nsites; ++i) {
+            double de = coef[5 * site_ids[i] + 4];
+            if (de != 0.0) {
+                cplx v = nops[i * DD + e];
+                h.x -= de * v.x;
+                h.y -= de * v.y;
+            }
+        }
+        for (int q = 0; q < ndriven; ++q) {
+            const double* c = coef + 5 * driven_ids[q];
+            const cplx* sx = dops + (3LL * q) * DD;
+            const cplx* sz = sx + DD;
+            const cplx* rp = sz + DD;
+            cplx vx = sx[e], vz = sz[e], vr = rp[e], vt = rp[et];
+            // W rp + conj(W) rp^H ; rp^H(a, b) = conj(rp(b, a))
+            h.x += c[0] * vx.x + c[1] * vz.x + (c[2] * vr.x - c[3] * vr.y) + (c[2] * vt.x - c[3] * vt.y);
+            h.y += c[0] * vx.y + c[1] * vz.y + (c[2] * vr.y + c[3] * vr.x) + (-c[2] * vt.y - c[3] * vt.x);
+        }
+        H[e] = h;
+    }
+}
+
+__global__ void check_finite_kernel(const cplx* x, long long n, int* flag) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        cplx v = x[e];
+        if (!isfinite(v.x) || !isfinite(v.y)) flag[0] = 1;
+    }
+}
+
+inline int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 4 * 152) g = 4 * 152;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+int red_blocks_for(long long n) {
+    long long g = (n + 2047) / 2048;
+    if (g > RED_BLOCKS) g = RED_BLOCKS;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+int k_norm2_partial(const cplx* x, long long n, double* partial, cudaStream_t s) {
+    int G = red_blocks_for(n);
+    norm2_partial_kernel<<<G, T, 0, s>>>(x, n, G, partial);
+    return 1;
+}
+
+int k_dots_partial(const cplx* V, long long ld, int nv, const cplx* w, long long n, cplx* partial,
+                   cudaStream_t s) {
+    int G = red_blocks_for(n);
+    dots_kernel<<<G, T, 0, s>>>(const_cast<cplx*>(V), ld, nv, w, n, G, partial, -1, nullptr, 0, -1);
+    return 1;
+}
+
+int k_dots_scaled(cplx* V, long long ld, int nv, const cplx* w, long long n, cplx* partial,
+                  int scale_col, const double* scale_src, long long skip_col, cudaStream_t s) {
+    int G = red_blocks_for(n);
+    dots_kernel<<<G, T, 0, s>>>(V, ld, nv, w, n, G, partial, scale_col, scale_src, 1, skip_col);
+    return 1;
+}
+
+int k_orth_update_ex(const cplx* V, long long ld, int nv, const cplx* partial_in, cplx* w, long long n,
+                     int mode, cplx* partial_dots, double* partial_norm, cplx* h_out, int accumulate,
+                     long long skip_col, cudaStream_t s) {
+    int G = red_blocks_for(n);
+    orth_update_kernel<<<G, T, 0, s>>>(V, ld, nv, partial_in, w, n, G, mode, partial_dots,
+                                       partial_norm, h_out, accumulate, skip_col);
+    return 1;
+}
+
+int k_scale_copy_dev(const cplx* x, long long n, const double* scale, cplx* y, cudaStream_t s) {
+    scale_copy_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scale, y);
+    return 1;
+}
+
+int k_combine(const cplx* V, long long ld, int nv, const KrylovScalars* ks, cplx* y, long long n,
+              cudaStream_t s) {
+    combine_kernel<<<grid_for(n), 256, 0, s>>>(V, ld, nv, ks, y, n);
+    return 1;
+}
+
+int k_krylov_start_ex(KrylovScalars* ks, const double* nrm2_partial, long long n, cudaStream_t s) {
+    krylov_start_kernel<<<1, 32, 0, s>>>(ks, nrm2_partial, red_blocks_for(n));
+    return 1;
+}
+
+int k_krylov_scalars_ex(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial,
+                        long long n, int j, double zr, double zi, double tol, cudaStream_t s) {
+    krylov_scalars_kernel<<<1, 32, 0, s>>>(ks, h1, h2, beta_partial, red_blocks_for(n), j, zr, zi, tol);
+    return 1;
+}
+
+int k_permute3(const cplx* x, cplx* y, int d0, int d1, int d2, int p0, int p1, int p2, int inverse,
+               cudaStream_t s) {
+    long long n = (long long)d0 * d1 * d2;
+    permute3_kernel<<<grid_for(n), 256, 0, s>>>(x, y, d0, d1, d2, p0, p1, p2, inverse);
+    return 1;
+}
+
+int k_fill(cplx* x, long long n, cplx v, cudaStream_t s) {
+    if (n <= 0) return 0;
+    fill_kernel<<<grid_for(n), 256, 0, s>>>(x, n, v);
+    return 1;
+}
+
+int k_assemble_block(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsites, const int* site_ids,
+                     const cplx* dops, int ndriven, const int* driven_ids, const double* coef,
+                     cudaStream_t s) {
+    long long DD = (long long)D * D;
+    assemble_block_kernel<<<grid_for(DD), 256, 0, s>>>(H, Hs, D, nops, nsites, site_ids, dops, ndriven,
+                                                       driven_ids, coef);
+    return 1;
+}
+
+int k_check_finite(const cplx* x, long long n, int* flag, cudaStream_t s) {
+    if (n <= 0) return 0;
+    check_finite_kernel<<<grid_for(n), 256, 0, s>>>(x, n, flag);
+    return 1;
+}

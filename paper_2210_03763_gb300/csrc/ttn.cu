@@ -1,0 +1,1525 @@
+// libttn host side: tree, environments, TDVP sweep and the C ABI (include/ttn.h).
+//
+// Method (Sec. "Tensor network simulations"): binary TTN over the
+// Hilbert-curve leaf order, single-site TDVP.  One step of dt is a forward
+// half-sweep with tau = dt/2 (post-order: for each child node, gauge move
+// down, recurse, QR back up and evolve the link backwards; then evolve the
+// node forwards) followed by its exact reverse.  H is frozen at t + dt/2.
+//
+// Every contraction is one launch of the strided complex GEMM (GemmArgs);
+// Lanczos, QR and the small tridiagonal exponential are in kernels.cu and
+// qr.cu.  All state lives on the device; the host only orders launches and
+// reads the Krylov convergence flag once per Lanczos step.
+#include "common.cuh"
+#include "../../include/ttn.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+int red_blocks_for(long long n);
+int k_dots_scaled(cplx* V, long long ld, int nv, const cplx* w, long long n, cplx* partial, int scale_col,
+                  const double* scale_src, long long skip_col, cudaStream_t s);
+int k_orth_update_ex(const cplx* V, long long ld, int nv, const cplx* partial_in, cplx* w, long long n,
+                     int mode, cplx* partial_dots, double* partial_norm, cplx* h_out, int accumulate,
+                     long long skip_col, cudaStream_t s);
+int k_scale_copy_dev(const cplx* x, long long n, const double* scale, cplx* y, cudaStream_t s);
+int k_krylov_start_ex(KrylovScalars* ks, const double* nrm2_partial, long long n, cudaStream_t s);
+int k_krylov_scalars_ex(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial,
+                        long long n, int j, double zr, double zi, double tol, cudaStream_t s);
+
+namespace {
+
+typedef std::complex<double> zc;
+constexpr int MAX_CHI = 256;
+constexpr int MAX_ATOMS = 1024;
+
+struct TtnError : std::runtime_error {
+    ttn_status code;
+    TtnError(ttn_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CUDA_OK(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            throw TtnError(TTN_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+inline cplx C(double re, double im = 0.0) { return make_double2(re, im); }
+
+// ------------------------------------------------------------------ tree
+struct Node {
+    int child[2];        // >= 0 node id, else -(leaf + 1)
+    int parent = -1;
+    int level = 0;
+    int d[3];
+    long long s = 0;
+    std::vector<int> sites;   // real atoms in the subtree, leaf order
+};
+
+// Hilbert curve on a side x side grid: cell visited at step d (own copy of
+// the iterative index -> (x, y) map, starting at the (0, 0) corner).
+void hilbert_cell(int side, int d, int& x, int& y) {
+    x = y = 0;
+    int t = d;
+    for (int s = 1; s < side; s *= 2) {
+        int rx = 1 & (t / 2);
+        int ry = 1 & (t ^ rx);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = s - 1 - x;
+                y = s - 1 - y;
+            }
+            std::swap(x, y);
+        }
+        x += s * rx;
+        y += s * ry;
+        t /= 4;
+    }
+}
+
+// ------------------------------------------------------------ environments
+// Environment of the atoms S behind one leg, in that leg's basis (dim D):
+// H = static block Hamiltonian (all n_i n_j terms inside S), n_i for every
+// atom of S, and (sx, sz, |r><1|) for the driven atoms of S.
+struct Env {
+    int D = 1;
+    std::vector<int> sites;
+    std::vector<int> driven;
+    bool has_H = false;            // false: static block is zero
+    cplx* H = nullptr;             // D*D
+    cplx* nops = nullptr;          // |sites| * D*D
+    cplx* dops = nullptr;          // 3 * |driven| * D*D
+    int* d_sites = nullptr;        // device copies of the id lists
+    int* d_driven = nullptr;
+    size_t cap_n = 0, cap_d = 0;   // capacity in matrices
+};
+
+struct Pair {  // channel side a (r = |S_a| channels), G side b
+    int a, b;
+    int r;
+    const cplx* Na;     // n ops of env a (r matrices of D_a^2)
+    cplx* G;            // r matrices of D_b^2 (filled per visit)
+};
+
+}  // namespace
+
+struct ttn_ctx {
+    int Lx = 0, Ly = 0, N = 0, chi = 0;
+    int n_leaves = 0;
+    std::vector<int> leaf_atom;
+    std::vector<Node> nodes;
+    int root = 0;
+    std::vector<std::vector<int>> level_nodes;
+    cudaStream_t stream = nullptr;
+    ttn_precision prec = TTN_FP64;
+    std::string err;
+    double t = 0.0;
+    int centre = -1;
+
+    std::vector<double> xy;
+    double C6 = 0.0, r_cut = 0.0;
+    std::vector<double> V;                 // N x N
+    std::vector<ttn_pulse> schedule;
+    std::vector<int> driven;               // per atom
+    double* d_coef = nullptr;              // 5 * N
+    std::vector<double> h_coef;
+
+    // device tensors: one buffer per node plus scratch, all of capacity smax
+    long long smax = 0;
+    std::vector<cplx*> T;
+    cplx* tmp[3] = {nullptr, nullptr, nullptr};
+    cplx* Z = nullptr;        // channel / op stack scratch
+    long long zcap = 0;       // capacity in complex
+    cplx* Gbuf[3] = {nullptr, nullptr, nullptr};
+    long long gcap = 0;
+    cplx* hb[3] = {nullptr, nullptr, nullptr};
+    cplx* Rbuf = nullptr;
+    cplx* Kbasis = nullptr;   // (KRYLOV_MMAX + 1) * smax
+    KrylovScalars* ks = nullptr;
+    cplx* kh1 = nullptr;      // KRYLOV_MMAX + 1
+    cplx* kh2 = nullptr;
+    cplx* kpart = nullptr;    // 2 * RED_BLOCKS * (KRYLOV_MMAX + 1)
+    double* kpn = nullptr;    // RED_BLOCKS
+    int* hflag = nullptr;     // pinned host: converged, nonfinite
+    QrScratch qr{};
+    std::map<std::pair<int, int>, int*> cand;   // (node, leg) -> candidate rows
+    std::map<std::pair<int, int>, int> ncand;
+
+    std::vector<Env> up, down, phys;
+    Env dummy;
+    std::map<std::pair<const Env*, const Env*>, cplx*> vsub;   // G-stack GEMM operands
+
+    int64_t stats[6] = {0, 0, 0, 0, 0, 0};
+    double max_err = 0.0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+void* dalloc(ttn_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) throw TtnError(TTN_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->allocs.push_back(p);
+    return p;
+}
+
+long long ipow3_capped(int k, long long cap) {
+    long long v = 1;
+    for (int i = 0; i < k; ++i) {
+        v *= 3;
+        if (v >= cap) return cap;
+    }
+    return v;
+}
+
+int leg_dim(const ttn_ctx* c, int k, int leg) { return c->nodes[k].d[leg]; }
+
+// ------------------------------------------------------------------ GEMMs
+void gemm(ttn_ctx* c, const GemmArgs& g) {
+    int n = -1;
+    if (c->prec == TTN_SPLIT_TF32X3) n = launch_zgemm_split(g, c->stream, nullptr, 0);
+    if (n < 0) n = launch_zgemm_f64(g, c->stream);
+    c->stats[3] += n;
+}
+
+GemmArgs base_args() {
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.Ki = g.Ko = g.Bi = g.Bo = 1;
+    g.alpha = C(1.0);
+    g.beta = C(0.0);
+    return g;
+}
+
+// Y = alpha * M x_leg X + beta * Y for nb stacked matrices M (stride m_bs) and
+// outputs (stride y_bs).  M is Dout x Din column-major; X has dims d with
+// d[leg] = Din; Y has dims d with d[leg] = Dout.
+void leg_apply(ttn_ctx* c, const cplx* M, int Dout, const cplx* X, const int* d, int leg, cplx* Y,
+               double beta, int nb = 1, long long m_bs = 0, long long y_bs = 0, bool conjM = false) {
+    GemmArgs g = base_args();
+    g.beta = C(beta);
+    int d0 = d[0], d1 = d[1], d2 = d[2];
+    int Din = d[leg];
+    g.conjA = g.conjB = 0;
+    if (leg == 0) {
+        g.M = Dout; g.N = d1 * d2; g.Ki = Din;
+        g.A = M; g.a_m = 1; g.a_ki = Dout; g.conjA = conjM;
+        g.B = X; g.b_ki = 1; g.b_n = d0;
+        g.C = Y; g.c_m = 1; g.c_n = Dout;
+        g.Bi = nb; g.a_bi = m_bs; g.b_bi = 0; g.c_bi = y_bs;
+    } else if (leg == 1) {
+        g.M = d0; g.N = Dout; g.Ki = Din;
+        g.A = X; g.a_m = 1; g.a_ki = d0; g.a_bi = (long long)d0 * d1;
+        g.B = M; g.b_ki = Dout; g.b_n = 1; g.conjB = conjM;
+        g.C = Y; g.c_m = 1; g.c_n = d0; g.c_bi = (long long)d0 * Dout;
+        g.Bi = d2;
+        g.Bo = nb; g.a_bo = 0; g.b_bo = m_bs; g.c_bo = y_bs;
+    } else {
+        g.M = d0 * d1; g.N = Dout; g.Ki = Din;
+        g.A = X; g.a_m = 1; g.a_ki = (long long)d0 * d1;
+        g.B = M; g.b_ki = Dout; g.b_n = 1; g.conjB = conjM;
+        g.C = Y; g.c_m = 1; g.c_n = (long long)d0 * d1;
+        g.Bi = nb; g.a_bi = 0; g.b_bi = m_bs; g.c_bi = y_bs;
+    }
+    gemm(c, g);
+}
+
+// Y += sum_i N_i x_a Z_i  (r channels; N_i square of dim d[a]; Z stack stride s)
+void channel_sum(ttn_ctx* c, const cplx* Nst, const cplx* Zst, const int* d, int a, int r, cplx* Y,
+                 double beta) {
+    GemmArgs g = base_args();
+    g.beta = C(beta);
+    int d0 = d[0], d1 = d[1], d2 = d[2];
+    long long s = (long long)d0 * d1 * d2;
+    int D = d[a];
+    long long DD = (long long)D * D;
+    g.Ko = r;
+    if (a == 0) {
+        g.M = d0; g.N = d1 * d2; g.Ki = d0;
+        g.A = Nst; g.a_m = 1; g.a_ki = D; g.a_ko = DD;
+        g.B = Zst; g.b_ki = 1; g.b_ko = s; g.b_n = d0;
+        g.C = Y; g.c_m = 1; g.c_n = d0;
+    } else if (a == 1) {
+        g.M = d0; g.N = d1; g.Ki = d1;
+        g.A = Zst; g.a_m = 1; g.a_ki = d0; g.a_ko = s; g.a_bi = (long long)d0 * d1;
+        g.B = Nst; g.b_ki = D; g.b_ko = DD; g.b_n = 1;
+        g.C = Y; g.c_m = 1; g.c_n = d0; g.c_bi = (long long)d0 * d1;
+        g.Bi = d2;
+    } else {
+        g.M = d0 * d1; g.N = d2; g.Ki = d2;
+        g.A = Zst; g.a_m = 1; g.a_ki = (long long)d0 * d1; g.a_ko = s;
+        g.B = Nst; g.b_ki = D; g.b_ko = DD; g.b_n = 1;
+        g.C = Y; g.c_m = 1; g.c_n = (long long)d0 * d1;
+    }
+    gemm(c, g);
+}
+
+// E_i = X^H W_i contracted over every leg except o (nb stacked W, stride s;
+// outputs stride d[o]^2).  Xh has dims dx, W dims dw (equal except leg o).
+void project(ttn_ctx* c, const cplx* X, const int* dx, const cplx* W, const int* dw, int o, cplx* E, int nb,
+             long long w_bs, long long e_bs) {
+    GemmArgs g = base_args();
+    g.conjA = 1;
+    int x0 = dx[0], x1 = dx[1];
+    if (o == 2) {
+        g.M = dx[2]; g.N = dw[2]; g.Ki = x0 * x1;
+        g.A = X; g.a_m = (long long)x0 * x1; g.a_ki = 1;
+        g.B = W; g.b_ki = 1; g.b_n = (long long)dw[0] * dw[1];
+        g.C = E; g.c_m = 1; g.c_n = dx[2];
+    } else if (o == 0) {
+        g.M = x0; g.N = dw[0]; g.Ki = dx[1] * dx[2];
+        g.A = X; g.a_m = 1; g.a_ki = x0;
+        g.B = W; g.b_ki = dw[0]; g.b_n = 1;
+        g.C = E; g.c_m = 1; g.c_n = x0;
+    } else {
+        g.M = x1; g.N = dw[1]; g.Ki = x0; g.Ko = dx[2];
+        g.A = X; g.a_m = x0; g.a_ki = 1; g.a_ko = (long long)x0 * x1;
+        g.B = W; g.b_ki = 1; g.b_ko = (long long)dw[0] * dw[1]; g.b_n = dw[0];
+        g.C = E; g.c_m = 1; g.c_n = x1;
+    }
+    g.Bi = nb; g.a_bi = 0; g.b_bi = w_bs; g.c_bi = e_bs;
+    gemm(c, g);
+}
+
+// ----------------------------------------------------------- env helpers
+const Env& env_of(ttn_ctx* c, int k, int leg) {
+    if (leg == 2) return k == c->root ? c->dummy : c->down[k];
+    int ch = c->nodes[k].child[leg];
+    return ch >= 0 ? c->up[ch] : c->phys[-ch - 1];
+}
+
+cplx* vsub_for(ttn_ctx* c, const Env& a, const Env& b) {
+    auto key = std::make_pair(&a, &b);
+    auto it = c->vsub.find(key);
+    if (it != c->vsub.end()) return it->second;
+    // B operand of the G-stack GEMM: |S_b| x |S_a|, element (j, i) = V(a_i, b_j)
+    size_t nb = b.sites.size(), na = a.sites.size();
+    std::vector<cplx> h(nb * na);
+    for (size_t i = 0; i < na; ++i)
+        for (size_t j = 0; j < nb; ++j) h[j + nb * i] = C(c->V[(size_t)a.sites[i] * c->N + b.sites[j]]);
+    cplx* d = (cplx*)dalloc(c, sizeof(cplx) * h.size());
+    CUDA_OK(cudaMemcpy(d, h.data(), sizeof(cplx) * h.size(), cudaMemcpyHostToDevice));
+    c->vsub[key] = d;
+    return d;
+}
+
+// G_i = sum_j V_ij n_j^(b) for every atom i of env a, into Gbuf
+void build_G(ttn_ctx* c, const Env& a, const Env& b, cplx* G) {
+    int r = (int)a.sites.size(), nbs = (int)b.sites.size();
+    long long DD = (long long)b.D * b.D;
+    GemmArgs g = base_args();
+    g.M = (int)DD; g.N = r; g.Ki = nbs;
+    g.A = b.nops; g.a_m = 1; g.a_ki = DD;
+    g.B = vsub_for(c, a, b); g.b_ki = 1; g.b_n = nbs;
+    g.C = G; g.c_m = 1; g.c_n = DD;
+    c->stats[3] += launch_zgemm_f64(g, c->stream);   // tiny, keep FP64
+}
+
+// Pairs of an effective Hamiltonian over envs e[0..2]; G stacks built.
+int setup_pairs(ttn_ctx* c, const Env* const* e, Pair* pairs) {
+    static const int PU[3] = {0, 0, 1}, PV[3] = {1, 2, 2};
+    int np = 0;
+    for (int p = 0; p < 3; ++p) {
+        const Env& eu = *e[PU[p]];
+        const Env& ev = *e[PV[p]];
+        if (eu.sites.empty() || ev.sites.empty()) continue;
+        bool uside = eu.sites.size() <= ev.sites.size();
+        const Env& ea = uside ? eu : ev;
+        const Env& eb = uside ? ev : eu;
+        Pair& P = pairs[np];
+        P.a = uside ? PU[p] : PV[p];
+        P.b = uside ? PV[p] : PU[p];
+        P.r = (int)ea.sites.size();
+        P.Na = ea.nops;
+        P.G = c->Gbuf[np];
+        build_G(c, ea, eb, P.G);
+        ++np;
+    }
+    return np;
+}
+
+// Y = H_eff X with block matrices hb[u] (nullptr: zero) and channel pairs.
+void heff_apply(ttn_ctx* c, const int* d, cplx* const* hb, const int* Dl, const Pair* pairs, int np,
+                const cplx* X, cplx* Y) {
+    double beta = 0.0;
+    for (int u = 0; u < 3; ++u) {
+        if (!hb[u]) continue;
+        leg_apply(c, hb[u], Dl[u], X, d, u, Y, beta);
+        beta = 1.0;
+    }
+    long long s = (long long)d[0] * d[1] * d[2];
+    for (int p = 0; p < np; ++p) {
+        const Pair& P = pairs[p];
+        if (P.r == 0) continue;
+        // Z_i = G_i x_b X for all i
+        long long DDb = (long long)d[P.b] * d[P.b];
+        leg_apply(c, P.G, d[P.b], X, d, P.b, c->Z, 0.0, P.r, DDb, s);
+        channel_sum(c, P.Na, c->Z, d, P.a, P.r, Y, beta);
+        beta = 1.0;
+    }
+    if (beta == 0.0) c->stats[3] += k_fill(Y, s, C(0.0), c->stream);
+}
+
+void assemble(ttn_ctx* c, const Env& e, cplx* out) {
+    c->stats[3] += k_assemble_block(out, e.has_H ? e.H : nullptr, e.D, e.nops, (int)e.sites.size(),
+                                    e.d_sites, e.dops, (int)e.driven.size(), e.d_driven, c->d_coef, c->stream);
+}
+
+bool env_has_block(const Env& e) { return e.has_H || !e.sites.empty(); }
+
+// --------------------------------------------------------------- Krylov
+// x <- exp(z H) x with H given by `apply`, Lanczos with full two-pass
+// re-orthogonalisation; z = (zr, zi).
+template <class F>
+void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
+    cudaStream_t s = c->stream;
+    const double tol = (c->prec == TTN_FP64) ? 1e-13 : 1e-9;
+    cplx* V = c->Kbasis;
+    const long long ld = n;
+    c->stats[3] += k_norm2_partial(x, n, c->kpn, s);
+    c->stats[3] += k_krylov_start_ex(c->ks, c->kpn, n, s);
+    c->stats[3] += k_scale_copy_dev(x, n, &c->ks->inv_scale, V, s);
+    int j = 0;
+    for (;; ++j) {
+        cplx* vj = V + (long long)j * ld;
+        cplx* w = V + (long long)(j + 1) * ld;
+        apply(vj, w);
+        c->stats[1] += 1;
+        c->stats[3] += k_dots_scaled(V, ld, j + 1, w, n, c->kpart, -1, nullptr, -1, s);
+        cplx* part2 = c->kpart + (size_t)RED_BLOCKS * (KRYLOV_MMAX + 1);
+        c->stats[3] += k_orth_update_ex(V, ld, j + 1, c->kpart, w, n, 1, part2, nullptr, c->kh1, 0, -1, s);
+        c->stats[3] += k_orth_update_ex(V, ld, j + 1, part2, w, n, 2, nullptr, c->kpn, c->kh2, 0, -1, s);
+        c->stats[3] += k_krylov_scalars_ex(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
+        CUDA_OK(cudaMemcpyAsync(c->hflag, &c->ks->converged, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaStreamSynchronize(s));
+        if (c->hflag[1]) throw TtnError(TTN_ERR_NUMERIC, "non-finite value in Lanczos");
+        if (c->hflag[0] || j == KRYLOV_MMAX - 1) break;
+        c->stats[3] += k_scale_copy_dev(w, n, &c->ks->inv_scale, w, s);
+    }
+    if (!c->hflag[0]) {
+        double err;
+        CUDA_OK(cudaMemcpy(&err, &c->ks->err, sizeof(double), cudaMemcpyDeviceToHost));
+        c->max_err = std::max(c->max_err, err);
+        if (err > 1e-6) throw TtnError(TTN_ERR_KRYLOV, "Lanczos did not converge in m_max steps");
+    }
+    c->stats[0] += 1;
+    c->stats[3] += k_combine(V, ld, j + 1, c->ks, x, n, s);
+}
+
+// ------------------------------------------------------ renormalisation
+void ensure_env_capacity(ttn_ctx* c, Env& E, size_t nn, size_t nd) {
+    long long DD = (long long)E.D * E.D;
+    if (!E.H) E.H = (cplx*)dalloc(c, sizeof(cplx) * DD);
+    if (nn > E.cap_n) {
+        E.nops = (cplx*)dalloc(c, sizeof(cplx) * DD * nn);
+        E.d_sites = (int*)dalloc(c, sizeof(int) * nn);
+        E.cap_n = nn;
+    }
+    if (nd > E.cap_d) {
+        E.dops = (cplx*)dalloc(c, sizeof(cplx) * DD * 3 * nd);
+        E.d_driven = (int*)dalloc(c, sizeof(int) * nd);
+        E.cap_d = nd;
+    }
+}
+
+// op stack (nop matrices of D_u^2) on leg u of X -> projected stack on leg o
+void renorm_stack(ttn_ctx* c, const cplx* X, const int* d, int u, int o, const cplx* ops, int nop, cplx* out) {
+    long long s = (long long)d[0] * d[1] * d[2];
+    long long DDu = (long long)d[u] * d[u], DDo = (long long)d[o] * d[o];
+    int chunk = (int)std::max<long long>(1, c->zcap / s);
+    for (int i0 = 0; i0 < nop; i0 += chunk) {
+        int nb = std::min(chunk, nop - i0);
+        leg_apply(c, ops + i0 * DDu, d[u], X, d, u, c->Z, 0.0, nb, DDu, s);
+        project(c, X, d, c->Z, d, o, out + i0 * DDo, nb, s, DDo);
+    }
+}
+
+// Environment seen through leg o of node tensor X (isometric w.r.t. o) from
+// the environments eu, ev of its other legs u < v.
+void renormalize(ttn_ctx* c, const cplx* X, const int* d, int o, const Env& eu, const Env& ev, Env& E) {
+    int u = (o == 0) ? 1 : 0, v = (o == 2) ? 1 : 2;
+    E.D = d[o];
+    E.sites = eu.sites;
+    E.sites.insert(E.sites.end(), ev.sites.begin(), ev.sites.end());
+    E.driven = eu.driven;
+    E.driven.insert(E.driven.end(), ev.driven.begin(), ev.driven.end());
+    ensure_env_capacity(c, E, E.sites.size(), E.driven.size());
+    long long DDo = (long long)E.D * E.D;
+    cudaStream_t s = c->stream;
+    if (!E.sites.empty())
+        CUDA_OK(cudaMemcpyAsync(E.d_sites, E.sites.data(), sizeof(int) * E.sites.size(), cudaMemcpyHostToDevice, s));
+    if (!E.driven.empty())
+        CUDA_OK(cudaMemcpyAsync(E.d_driven, E.driven.data(), sizeof(int) * E.driven.size(), cudaMemcpyHostToDevice, s));
+    // static block: X^H (Hs_u + Hs_v + sum V n n) X
+    const Env* e3[3];
+    e3[u] = &eu;
+    e3[v] = &ev;
+    e3[o] = &c->dummy;
+    cplx* hbs[3] = {nullptr, nullptr, nullptr};
+    int Dl[3] = {d[0], d[1], d[2]};
+    if (eu.has_H) hbs[u] = eu.H;
+    if (ev.has_H) hbs[v] = ev.H;
+    Pair pairs[3];
+    int np = 0;
+    if (!eu.sites.empty() && !ev.sites.empty()) {
+        // only the (u, v) pair
+        bool uside = eu.sites.size() <= ev.sites.size();
+        const Env& ea = uside ? eu : ev;
+        const Env& eb = uside ? ev : eu;
+        pairs[0].a = uside ? u : v;
+        pairs[0].b = uside ? v : u;
+        pairs[0].r = (int)ea.sites.size();
+        pairs[0].Na = ea.nops;
+        pairs[0].G = c->Gbuf[0];
+        build_G(c, ea, eb, pairs[0].G);
+        np = 1;
+    }
+    (void)e3;
+    E.has_H = (hbs[u] || hbs[v] || np > 0);
+    if (E.has_H) {
+        cplx* W = c->tmp[2];
+        heff_apply(c, d, hbs, Dl, pairs, np, X, W);
+        project(c, X, d, W, d, o, E.H, 1, 0, 0);
+    }
+    // one-site operators
+    renorm_stack(c, X, d, u, o, eu.nops, (int)eu.sites.size(), E.nops);
+    renorm_stack(c, X, d, v, o, ev.nops, (int)ev.sites.size(), E.nops + eu.sites.size() * DDo);
+    renorm_stack(c, X, d, u, o, eu.dops, 3 * (int)eu.driven.size(), E.dops);
+    renorm_stack(c, X, d, v, o, ev.dops, 3 * (int)ev.driven.size(), E.dops + 3 * eu.driven.size() * DDo);
+}
+
+void build_up(ttn_ctx* c, int k) {
+    const Node& nd = c->nodes[k];
+    renormalize(c, c->T[k], nd.d, 2, env_of(c, k, 0), env_of(c, k, 1), c->up[k]);
+}
+
+void build_down(ttn_ctx* c, int k, int leg) {
+    int ch = c->nodes[k].child[leg];
+    int other = 1 - leg;
+    const Env& e_other = env_of(c, k, other);
+    const Env& e_par = env_of(c, k, 2);
+    renormalize(c, c->T[k], c->nodes[k].d, leg, leg == 0 ? e_other : e_other, e_par, c->down[ch]);
+}
+
+void rebuild_up_envs(ttn_ctx* c) {
+    for (auto& lev : c->level_nodes)
+        for (int k : lev)
+            if (k != c->root) build_up(c, k);
+}
+
+// ----------------------------------------------------------- QR & moves
+// X (node k) = Q x_o R; Q replaces the node tensor, R (D x D) into Rbuf.
+void qr_leg(ttn_ctx* c, int k, int o) {
+    const Node& nd = c->nodes[k];
+    int D = nd.d[o];
+    long long s = nd.s, M = s / D;
+    cplx* A = c->T[k];
+    static const int PERM[3][3] = {{1, 2, 0}, {0, 2, 1}, {0, 1, 2}};
+    if (o != 2) {
+        c->stats[3] += k_permute3(c->T[k], c->tmp[0], nd.d[0], nd.d[1], nd.d[2], PERM[o][0], PERM[o][1],
+                                  PERM[o][2], 0, c->stream);
+        A = c->tmp[0];
+    }
+    int ndep = 0;
+    auto key = std::make_pair(k, o);
+    c->stats[3] += qr_cgs2(A, (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep);
+    c->stats[4] += 1;
+    c->stats[5] += ndep;
+    if (o != 2)
+        c->stats[3] += k_permute3(c->tmp[0], c->T[k], nd.d[0], nd.d[1], nd.d[2], PERM[o][0], PERM[o][1],
+                                  PERM[o][2], 1, c->stream);
+}
+
+// node k <- Rbuf x_leg node k   (absorb the link matrix)
+void absorb(ttn_ctx* c, int k, int leg) {
+    const Node& nd = c->nodes[k];
+    leg_apply(c, c->Rbuf, nd.d[leg], c->T[k], nd.d, leg, c->tmp[1], 0.0);
+    std::swap(c->T[k], c->tmp[1]);
+}
+
+void node_evolve(ttn_ctx* c, int k, double tau) {
+    const Node& nd = c->nodes[k];
+    const Env* e[3] = {&env_of(c, k, 0), &env_of(c, k, 1), &env_of(c, k, 2)};
+    cplx* hbs[3];
+    int Dl[3] = {nd.d[0], nd.d[1], nd.d[2]};
+    for (int u = 0; u < 3; ++u) {
+        hbs[u] = nullptr;
+        if (env_has_block(*e[u])) {
+            assemble(c, *e[u], c->hb[u]);
+            hbs[u] = c->hb[u];
+        }
+    }
+    Pair pairs[3];
+    int np = setup_pairs(c, e, pairs);
+    krylov(c, c->T[k], nd.s, 0.0, -tau, [&](const cplx* x, cplx* y) { heff_apply(c, nd.d, hbs, Dl, pairs, np, x, y); });
+}
+
+// R <- exp(+i tau H_link) R, rows in basis of er, columns of ec
+void link_evolve(ttn_ctx* c, const Env& er, const Env& ec, double tau) {
+    int d[3] = {er.D, ec.D, 1};
+    const Env* e[3] = {&er, &ec, &c->dummy};
+    cplx* hbs[3] = {nullptr, nullptr, nullptr};
+    int Dl[3] = {d[0], d[1], 1};
+    for (int u = 0; u < 2; ++u)
+        if (env_has_block(*e[u])) {
+            assemble(c, *e[u], c->hb[u]);
+            hbs[u] = c->hb[u];
+        }
+    Pair pairs[3];
+    int np = setup_pairs(c, e, pairs);
+    krylov(c, c->Rbuf, (long long)d[0] * d[1], 0.0, tau,
+           [&](const cplx* x, cplx* y) { heff_apply(c, d, hbs, Dl, pairs, np, x, y); });
+}
+
+std::vector<std::pair<int, int>> node_children(const ttn_ctx* c, int k) {
+    std::vector<std::pair<int, int>> out;
+    for (int u = 0; u < 2; ++u)
+        if (c->nodes[k].child[u] >= 0) out.push_back({u, c->nodes[k].child[u]});
+    return out;
+}
+
+void sweep_fwd(ttn_ctx* c, int k, double tau) {
+    for (auto [u, ch] : node_children(c, k)) {
+        qr_leg(c, k, u);
+        build_down(c, k, u);
+        absorb(c, ch, 2);
+        sweep_fwd(c, ch, tau);
+        qr_leg(c, ch, 2);
+        build_up(c, ch);
+        link_evolve(c, c->up[ch], c->down[ch], tau);
+        absorb(c, k, u);
+    }
+    node_evolve(c, k, tau);
+}
+
+void sweep_rev(ttn_ctx* c, int k, double tau) {
+    node_evolve(c, k, tau);
+    auto ch_list = node_children(c, k);
+    for (auto it = ch_list.rbegin(); it != ch_list.rend(); ++it) {
+        auto [u, ch] = *it;
+        qr_leg(c, k, u);
+        build_down(c, k, u);
+        link_evolve(c, c->down[ch], c->up[ch], tau);
+        absorb(c, ch, 2);
+        sweep_rev(c, ch, tau);
+        qr_leg(c, ch, 2);
+        build_up(c, ch);
+        absorb(c, k, u);
+    }
+}
+
+// Move the orthogonality centre from the root down to node k (gauge only).
+void centre_to(ttn_ctx* c, int k) {
+    std::vector<int> path;
+    for (int x = k; x != c->root; x = c->nodes[x].parent) path.push_back(x);
+    std::reverse(path.begin(), path.end());
+    int cur = c->root;
+    for (int ch : path) {
+        int u = c->nodes[cur].child[0] == ch ? 0 : 1;
+        qr_leg(c, cur, u);
+        build_down(c, cur, u);
+        absorb(c, ch, 2);
+        cur = ch;
+    }
+    c->centre = k;
+}
+
+void centre_to_root(ttn_ctx* c) {
+    if (c->centre == c->root || c->centre < 0) {
+        c->centre = c->root;
+        return;
+    }
+    int cur = c->centre;
+    while (cur != c->root) {
+        int par = c->nodes[cur].parent;
+        int u = c->nodes[par].child[0] == cur ? 0 : 1;
+        qr_leg(c, cur, 2);
+        build_up(c, cur);
+        absorb(c, par, u);
+        cur = par;
+    }
+    c->centre = c->root;
+}
+
+// ---------------------------------------------------------------- setup
+void compute_coef(ttn_ctx* c, double t) {
+    std::fill(c->h_coef.begin(), c->h_coef.end(), 0.0);
+    for (const ttn_pulse& p : c->schedule) {
+        if (p.t0 <= t && t < p.t1) {
+            double* q = &c->h_coef[5 * p.atom];
+            q[0] += p.omega_x;
+            q[1] += p.omega_z;
+            q[2] += p.omega_r * std::cos(p.phase_r);
+            q[3] += p.omega_r * std::sin(p.phase_r);
+            q[4] += p.delta;
+        }
+    }
+    CUDA_OK(cudaMemcpyAsync(c->d_coef, c->h_coef.data(), sizeof(double) * c->h_coef.size(),
+                            cudaMemcpyHostToDevice, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));   // h_coef is reused on the next call
+}
+
+void set_phys_envs(ttn_ctx* c) {
+    static const double NR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 1};
+    for (int l = 0; l < c->n_leaves; ++l) {
+        Env& E = c->phys[l];
+        E.D = 3;
+        E.has_H = false;
+        int a = c->leaf_atom[l];
+        E.sites.clear();
+        E.driven.clear();
+        if (a < 0) continue;
+        E.sites.push_back(a);
+        if (c->driven[a]) E.driven.push_back(a);
+        ensure_env_capacity(c, E, 1, 1);
+        // column-major 3x3: element (r, col) at r + 3 col
+        cplx n[9], ops[27];
+        for (int i = 0; i < 9; ++i) n[i] = C(NR[i]);
+        for (int i = 0; i < 27; ++i) ops[i] = C(0.0);
+        ops[1 + 3 * 0] = C(1.0);  // sx: |1><0|
+        ops[0 + 3 * 1] = C(1.0);  // sx: |0><1|
+        ops[9 + 0] = C(1.0);      // sz (0,0)
+        ops[9 + 4] = C(-1.0);     // sz (1,1)
+        ops[18 + 2 + 3 * 1] = C(1.0);   // |r><1|: (2, 1)
+        CUDA_OK(cudaMemcpy(E.nops, n, sizeof(n), cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(E.dops, ops, sizeof(ops), cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(E.d_sites, &a, sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(E.d_driven, &a, sizeof(int), cudaMemcpyHostToDevice));
+    }
+}
+
+// candidate rows (a + da*b), ordered by (a + b, a), for QR of node k w.r.t. leg o
+void build_candidates(ttn_ctx* c) {
+    for (int k = 0; k < (int)c->nodes.size(); ++k) {
+        const Node& nd = c->nodes[k];
+        for (int o = 0; o < 3; ++o) {
+            int la = (o == 0) ? 1 : 0, lb = (o == 2) ? 1 : 2;
+            int da = nd.d[la], db = nd.d[lb];
+            auto allowed = [&](int leg, int idx) {
+                if (leg == 2) return true;
+                int ch = nd.child[leg];
+                if (ch >= 0) return true;
+                return c->leaf_atom[-ch - 1] >= 0 || idx == 0;
+            };
+            std::vector<std::pair<std::pair<int, int>, int>> rows;
+            for (int b = 0; b < db; ++b)
+                for (int a = 0; a < da; ++a)
+                    if (allowed(la, a) && allowed(lb, b)) rows.push_back({{a + b, a}, a + da * b});
+            std::sort(rows.begin(), rows.end());
+            std::vector<int> h(rows.size());
+            for (size_t i = 0; i < rows.size(); ++i) h[i] = rows[i].second;
+            int* d = (int*)dalloc(c, sizeof(int) * std::max<size_t>(1, h.size()));
+            if (!h.empty()) CUDA_OK(cudaMemcpy(d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice));
+            c->cand[{k, o}] = d;
+            c->ncand[{k, o}] = (int)h.size();
+        }
+    }
+}
+
+void build_tree(ttn_ctx* c) {
+    int side = 1;
+    while (side < std::max(c->Lx, c->Ly)) side *= 2;
+    c->leaf_atom.clear();
+    for (int d = 0; d < side * side; ++d) {
+        int x, y;
+        hilbert_cell(side, d, x, y);
+        if (x < c->Lx && y < c->Ly) c->leaf_atom.push_back(x + c->Lx * y);
+    }
+    int nl = 2;
+    while (nl < (int)c->leaf_atom.size()) nl *= 2;
+    c->leaf_atom.resize(nl, -1);
+    c->n_leaves = nl;
+    c->nodes.clear();
+    c->level_nodes.clear();
+    std::vector<int> cur;
+    for (int i = 0; i < nl / 2; ++i) {
+        Node nd;
+        nd.child[0] = -(2 * i) - 1;
+        nd.child[1] = -(2 * i + 1) - 1;
+        nd.level = 0;
+        for (int l = 2 * i; l <= 2 * i + 1; ++l)
+            if (c->leaf_atom[l] >= 0) nd.sites.push_back(c->leaf_atom[l]);
+        cur.push_back((int)c->nodes.size());
+        c->nodes.push_back(nd);
+    }
+    c->level_nodes.push_back(cur);
+    int lev = 0;
+    while (cur.size() > 1) {
+        ++lev;
+        std::vector<int> nxt;
+        for (size_t i = 0; i < cur.size() / 2; ++i) {
+            Node nd;
+            nd.child[0] = cur[2 * i];
+            nd.child[1] = cur[2 * i + 1];
+            nd.level = lev;
+            int id = (int)c->nodes.size();
+            for (int u = 0; u < 2; ++u) {
+                c->nodes[nd.child[u]].parent = id;
+                const auto& cs = c->nodes[nd.child[u]].sites;
+                nd.sites.insert(nd.sites.end(), cs.begin(), cs.end());
+            }
+            nxt.push_back(id);
+            c->nodes.push_back(nd);
+        }
+        cur = nxt;
+        c->level_nodes.push_back(cur);
+    }
+    c->root = cur[0];
+    // bond dims
+    std::vector<int> pdim(c->nodes.size(), 1);
+    for (int k = 0; k < (int)c->nodes.size(); ++k) {
+        if (k == c->root) continue;
+        int a = (int)c->nodes[k].sites.size();
+        long long cap = c->chi + 1;
+        pdim[k] = (int)std::min<long long>(c->chi, std::min(ipow3_capped(a, cap), ipow3_capped(c->N - a, cap)));
+    }
+    c->smax = 1;
+    for (int k = 0; k < (int)c->nodes.size(); ++k) {
+        Node& nd = c->nodes[k];
+        for (int u = 0; u < 2; ++u) nd.d[u] = nd.child[u] >= 0 ? pdim[nd.child[u]] : 3;
+        nd.d[2] = pdim[k];
+        nd.s = (long long)nd.d[0] * nd.d[1] * nd.d[2];
+        c->smax = std::max(c->smax, nd.s);
+    }
+}
+
+void allocate(ttn_ctx* c) {
+    int nn = (int)c->nodes.size();
+    c->T.assign(nn, nullptr);
+    for (int k = 0; k < nn; ++k) c->T[k] = (cplx*)dalloc(c, sizeof(cplx) * c->smax);
+    for (int i = 0; i < 3; ++i) c->tmp[i] = (cplx*)dalloc(c, sizeof(cplx) * c->smax);
+    // channel scratch: max over nodes of r * s, at least 8 * smax for op stacks
+    long long zc = 8 * c->smax;
+    long long gc = 1;
+    for (int k = 0; k < nn; ++k) {
+        const Node& nd = c->nodes[k];
+        long long tot = c->N;
+        long long in0 = (nd.child[0] >= 0) ? (long long)c->nodes[nd.child[0]].sites.size() : 1;
+        long long in1 = (nd.child[1] >= 0) ? (long long)c->nodes[nd.child[1]].sites.size() : 1;
+        long long out = tot - (long long)nd.sites.size();
+        long long r = std::max({std::min(in0, in1), std::min(in0, out), std::min(in1, out)});
+        zc = std::max(zc, r * nd.s);
+        int Dm = std::max({nd.d[0], nd.d[1], nd.d[2]});
+        gc = std::max(gc, std::max(r, (long long)c->N) * (long long)Dm * Dm);
+    }
+    c->zcap = zc;
+    c->Z = (cplx*)dalloc(c, sizeof(cplx) * zc);
+    c->gcap = gc;
+    for (int i = 0; i < 3; ++i) c->Gbuf[i] = (cplx*)dalloc(c, sizeof(cplx) * gc);
+    for (int i = 0; i < 3; ++i) c->hb[i] = (cplx*)dalloc(c, sizeof(cplx) * MAX_CHI * MAX_CHI);
+    c->Rbuf = (cplx*)dalloc(c, sizeof(cplx) * MAX_CHI * MAX_CHI);
+    c->Kbasis = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1) * c->smax);
+    c->ks = (KrylovScalars*)dalloc(c, sizeof(KrylovScalars));
+    c->kh1 = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1));
+    c->kh2 = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1));
+    c->kpart = (cplx*)dalloc(c, sizeof(cplx) * 2 * RED_BLOCKS * (MAX_CHI + 2));
+    c->kpn = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
+    c->qr.part = (cplx*)dalloc(c, sizeof(cplx) * 2 * RED_BLOCKS * (MAX_CHI + 2));
+    c->qr.h = (cplx*)dalloc(c, sizeof(cplx) * (MAX_CHI + 2));
+    c->qr.pnorm = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
+    c->qr.scal = (double*)dalloc(c, sizeof(double) * 8);
+    c->qr.flags = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
+    c->qr.rownorm = (double*)dalloc(c, sizeof(double) * c->smax);
+    c->qr.pick = (int*)dalloc(c, sizeof(int) * 4);
+    c->d_coef = (double*)dalloc(c, sizeof(double) * 5 * c->N);
+    c->h_coef.assign(5 * c->N, 0.0);
+    CUDA_OK(cudaMallocHost(&c->hflag, 4 * sizeof(int)));
+    c->up.assign(nn, Env());
+    c->down.assign(nn, Env());
+    c->phys.assign(c->n_leaves, Env());
+    c->dummy = Env();
+    c->dummy.D = 1;
+    for (int k = 0; k < nn; ++k) {
+        c->up[k].D = c->nodes[k].d[2];
+        c->down[k].D = c->nodes[k].d[2];
+    }
+}
+
+// Build node tensors from per-leaf branch vectors (3 x nb, column-major) and
+// the root combination: every node is the QR-completed isometry of its
+// branch columns (the same completion rule as the sweep's QR).
+void build_from_branches(ttn_ctx* c, const std::vector<std::vector<zc>>& leaf_br, int nb,
+                         const std::vector<zc>& root_coef) {
+    int nn = (int)c->nodes.size();
+    std::vector<std::vector<zc>> B(nn);   // per node: d2 x nb branch coordinates
+    for (auto& lev : c->level_nodes) {
+        for (int k : lev) {
+            const Node& nd = c->nodes[k];
+            const std::vector<zc>* col[2];
+            int dd[2] = {nd.d[0], nd.d[1]};
+            for (int u = 0; u < 2; ++u) {
+                int ch = nd.child[u];
+                col[u] = ch >= 0 ? &B[ch] : &leaf_br[-ch - 1];
+            }
+            long long M = (long long)dd[0] * dd[1];
+            int D = nd.d[2];
+            std::vector<zc> A(M * std::max(D, nb), zc(0.0));
+            std::vector<zc> full(M * nb);
+            for (int b = 0; b < nb; ++b)
+                for (int j = 0; j < dd[1]; ++j)
+                    for (int i = 0; i < dd[0]; ++i)
+                        full[i + dd[0] * j + M * b] = (*col[0])[i + dd[0] * b] * (*col[1])[j + dd[1] * b];
+            if (k == c->root) {
+                std::vector<zc> X(M, zc(0.0));
+                for (int b = 0; b < nb; ++b)
+                    for (long long e = 0; e < M; ++e) X[e] += full[e + M * b] * root_coef[b];
+                CUDA_OK(cudaMemcpy(c->T[k], X.data(), sizeof(cplx) * M, cudaMemcpyHostToDevice));
+                continue;
+            }
+            int nk = std::min(nb, D);
+            std::fill(A.begin(), A.end(), zc(0.0));
+            for (long long e = 0; e < M * nk; ++e) A[e] = full[e];
+            CUDA_OK(cudaMemcpy(c->T[k], A.data(), sizeof(cplx) * M * D, cudaMemcpyHostToDevice));
+            int ndep = 0;
+            auto key = std::make_pair(k, 2);
+            qr_cgs2(c->T[k], (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep);
+            std::vector<zc> R((size_t)D * D), Q(M * D);
+            CUDA_OK(cudaMemcpyAsync(R.data(), c->Rbuf, sizeof(cplx) * D * D, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_OK(cudaMemcpyAsync(Q.data(), c->T[k], sizeof(cplx) * M * D, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_OK(cudaStreamSynchronize(c->stream));
+            std::vector<zc> Bk((size_t)D * nb, zc(0.0));
+            if (nb <= D) {
+                for (int b = 0; b < nb; ++b)
+                    for (int r = 0; r < D; ++r) Bk[r + D * b] = R[r + D * b];
+            } else {
+                for (int b = 0; b < nb; ++b)
+                    for (int r = 0; r < D; ++r) {
+                        zc s(0.0);
+                        for (long long e = 0; e < M; ++e) s += std::conj(Q[e + M * r]) * full[e + M * b];
+                        Bk[r + D * b] = s;
+                    }
+            }
+            B[k] = Bk;
+        }
+    }
+    c->centre = c->root;
+    rebuild_up_envs(c);
+}
+
+void set_driven(ttn_ctx* c) {
+    c->driven.assign(c->N, 0);
+    for (const ttn_pulse& p : c->schedule)
+        if (p.omega_x != 0.0 || p.omega_z != 0.0 || p.omega_r != 0.0) c->driven[p.atom] = 1;
+}
+
+void set_V(ttn_ctx* c) {
+    int N = c->N;
+    c->V.assign((size_t)N * N, 0.0);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            if (i == j) continue;
+            double dx = c->xy[2 * i] - c->xy[2 * j], dy = c->xy[2 * i + 1] - c->xy[2 * j + 1];
+            double d = std::hypot(dx, dy);
+            if (c->r_cut > 0 && d > c->r_cut) continue;
+            c->V[(size_t)i * N + j] = c->C6 / std::pow(d, 6);
+        }
+    c->vsub.clear();   // device buffers stay owned by allocs
+}
+
+// ------------------------------------------------------------- observables
+// <psi| op_i |psi> for ops renormalised to the root legs (centre at root).
+void root_expect(ttn_ctx* c, const cplx* st0, int n0, const cplx* st1, int n1, std::vector<zc>& out) {
+    const Node& nd = c->nodes[c->root];
+    long long s = nd.s;
+    out.assign(n0 + n1, zc(0.0));
+    cplx* res = c->Gbuf[2];
+    const cplx* st[2] = {st0, st1};
+    int ns[2] = {n0, n1};
+    int off = 0;
+    for (int u = 0; u < 2; ++u) {
+        if (ns[u] == 0) continue;
+        long long DD = (long long)nd.d[u] * nd.d[u];
+        int chunk = (int)std::max<long long>(1, c->zcap / s);
+        for (int i0 = 0; i0 < ns[u]; i0 += chunk) {
+            int nb = std::min(chunk, ns[u] - i0);
+            leg_apply(c, st[u] + i0 * DD, nd.d[u], c->T[c->root], nd.d, u, c->Z, 0.0, nb, DD, s);
+            project(c, c->T[c->root], nd.d, c->Z, nd.d, 2, res + off + i0, nb, s, 1);
+        }
+        off += ns[u];
+    }
+    std::vector<cplx> h(n0 + n1);
+    CUDA_OK(cudaMemcpyAsync(h.data(), res, sizeof(cplx) * (n0 + n1), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n0 + n1; ++i) out[i] = zc(h[i].x, h[i].y);
+}
+
+double root_norm(ttn_ctx* c) {
+    const Node& nd = c->nodes[c->root];
+    project(c, c->T[c->root], nd.d, c->T[c->root], nd.d, 2, c->Gbuf[2], 1, 0, 0);
+    cplx h;
+    CUDA_OK(cudaMemcpyAsync(&h, c->Gbuf[2], sizeof(cplx), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    return h.x;
+}
+
+// Renormalise one diagonal one-site operator (per atom) up to the root legs.
+void measure_projector(ttn_ctx* c, int level_index, std::vector<double>& out) {
+    // bare operator: |level><level|
+    cplx bare[9];
+    for (int i = 0; i < 9; ++i) bare[i] = C(0.0);
+    bare[level_index * 4] = C(1.0);
+    int nn = (int)c->nodes.size();
+    std::vector<cplx*> stack(nn, nullptr);
+    std::vector<std::vector<int>> sites(nn);
+    cplx* dbare = c->Gbuf[1];
+    CUDA_OK(cudaMemcpyAsync(dbare, bare, sizeof(bare), cudaMemcpyHostToDevice, c->stream));
+    std::vector<void*> temp;
+    for (auto& lev : c->level_nodes)
+        for (int k : lev) {
+            if (k == c->root) continue;
+            const Node& nd = c->nodes[k];
+            long long DDo = (long long)nd.d[2] * nd.d[2];
+            cplx* st = nullptr;
+            CUDA_OK(cudaMalloc(&st, sizeof(cplx) * DDo * std::max<size_t>(1, nd.sites.size())));
+            temp.push_back(st);
+            long long off = 0;
+            for (int u = 0; u < 2; ++u) {
+                int ch = nd.child[u];
+                if (ch < 0) {
+                    if (c->leaf_atom[-ch - 1] < 0) continue;
+                    renorm_stack(c, c->T[k], nd.d, u, 2, dbare, 1, st + off * DDo);
+                    sites[k].push_back(c->leaf_atom[-ch - 1]);
+                    off += 1;
+                } else {
+                    int n = (int)sites[ch].size();
+                    renorm_stack(c, c->T[k], nd.d, u, 2, stack[ch], n, st + off * DDo);
+                    sites[k].insert(sites[k].end(), sites[ch].begin(), sites[ch].end());
+                    off += n;
+                }
+            }
+            stack[k] = st;
+        }
+    const Node& rn = c->nodes[c->root];
+    const cplx* st[2];
+    int ns[2];
+    std::vector<int> order;
+    std::vector<cplx*> extra;
+    for (int u = 0; u < 2; ++u) {
+        int ch = rn.child[u];
+        if (ch >= 0) {
+            st[u] = stack[ch];
+            ns[u] = (int)sites[ch].size();
+            order.insert(order.end(), sites[ch].begin(), sites[ch].end());
+        } else {
+            int a = c->leaf_atom[-ch - 1];
+            st[u] = dbare;
+            ns[u] = a >= 0 ? 1 : 0;
+            if (a >= 0) order.push_back(a);
+        }
+    }
+    std::vector<zc> vals;
+    root_expect(c, st[0], ns[0], st[1], ns[1], vals);
+    out.assign(c->N, 0.0);
+    for (size_t i = 0; i < order.size(); ++i) out[order[i]] = vals[i].real();
+    for (void* p : temp) cudaFree(p);
+}
+
+zc overlap(ttn_ctx* psi, const ttn_ctx* tgt) {
+    ttn_ctx* c = psi;
+    int nn = (int)c->nodes.size();
+    std::vector<cplx*> M(nn, nullptr);
+    std::vector<void*> temp;
+    for (auto& lev : c->level_nodes)
+        for (int k : lev) {
+            const Node& nd = c->nodes[k];
+            const Node& nt = tgt->nodes[k];
+            // W = M_c0 x_0 psi_k, then M_c1 x_1 W
+            const cplx* cur = c->T[k];
+            int d[3] = {nd.d[0], nd.d[1], nd.d[2]};
+            cplx* bufs[2] = {c->tmp[0], c->tmp[1]};
+            int bi = 0;
+            for (int u = 0; u < 2; ++u) {
+                int ch = nd.child[u];
+                if (ch < 0) continue;
+                leg_apply(c, M[ch], nt.d[u], cur, d, u, bufs[bi], 0.0);
+                d[u] = nt.d[u];
+                cur = bufs[bi];
+                bi ^= 1;
+            }
+            cplx* out = nullptr;
+            CUDA_OK(cudaMalloc(&out, sizeof(cplx) * (size_t)nt.d[2] * nd.d[2]));
+            temp.push_back(out);
+            project(c, tgt->T[k], nt.d, cur, d, 2, out, 1, 0, 0);
+            M[k] = out;
+        }
+    cplx h;
+    CUDA_OK(cudaMemcpyAsync(&h, M[c->root], sizeof(cplx), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    for (void* p : temp) cudaFree(p);
+    return zc(h.x, h.y);
+}
+
+double energy(ttn_ctx* c) {
+    compute_coef(c, c->t);
+    int k = c->root;
+    const Node& nd = c->nodes[k];
+    const Env* e[3] = {&env_of(c, k, 0), &env_of(c, k, 1), &env_of(c, k, 2)};
+    cplx* hbs[3] = {nullptr, nullptr, nullptr};
+    int Dl[3] = {nd.d[0], nd.d[1], nd.d[2]};
+    for (int u = 0; u < 3; ++u)
+        if (env_has_block(*e[u])) {
+            assemble(c, *e[u], c->hb[u]);
+            hbs[u] = c->hb[u];
+        }
+    Pair pairs[3];
+    int np = setup_pairs(c, e, pairs);
+    heff_apply(c, nd.d, hbs, Dl, pairs, np, c->T[k], c->tmp[2]);
+    project(c, c->T[k], nd.d, c->tmp[2], nd.d, 2, c->Gbuf[2], 1, 0, 0);
+    cplx h;
+    CUDA_OK(cudaMemcpyAsync(&h, c->Gbuf[2], sizeof(cplx), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    return h.x;
+}
+
+void sync_check(ttn_ctx* c) {
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    CUDA_OK(cudaGetLastError());
+}
+
+template <class F>
+ttn_status guard(ttn_ctx* c, F f) {
+    try {
+        f();
+        return TTN_OK;
+    } catch (const TtnError& e) {
+        if (c) c->err = e.what();
+        return e.code;
+    } catch (const std::exception& e) {
+        if (c) c->err = e.what();
+        return TTN_ERR_ALLOC;
+    }
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+ttn_status ttn_create(int Lx, int Ly, int levels, int chi, ttn_ctx** out) {
+    if (!out) return TTN_ERR_ARG;
+    *out = nullptr;
+    if (levels != 3 || chi < 1 || chi > MAX_CHI || Lx < 1 || Ly < 1 || (long long)Lx * Ly > MAX_ATOMS)
+        return TTN_ERR_ARG;
+    ttn_ctx* c = new ttn_ctx();
+    c->Lx = Lx;
+    c->Ly = Ly;
+    c->N = Lx * Ly;
+    c->chi = chi;
+    ttn_status st = guard(c, [&] {
+        build_tree(c);
+        allocate(c);
+        build_candidates(c);
+        c->xy.resize(2 * c->N);
+        for (int i = 0; i < c->N; ++i) {
+            c->xy[2 * i] = i % Lx;
+            c->xy[2 * i + 1] = i / Lx;
+        }
+        c->C6 = 0.0;
+        set_V(c);
+        c->driven.assign(c->N, 0);
+        set_phys_envs(c);
+        std::vector<std::vector<zc>> lb(c->n_leaves, std::vector<zc>{1.0, 0.0, 0.0});
+        build_from_branches(c, lb, 1, {zc(1.0)});
+        sync_check(c);
+    });
+    if (st != TTN_OK) {
+        fprintf(stderr, "ttn_create: %s\n", c->err.c_str());
+        ttn_destroy(c);
+        return st;
+    }
+    *out = c;
+    return TTN_OK;
+}
+
+void ttn_destroy(ttn_ctx* c) {
+    if (!c) return;
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->hflag) cudaFreeHost(c->hflag);
+    delete c;
+}
+
+const char* ttn_last_error(const ttn_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ttn_status ttn_set_stream(ttn_ctx* c, void* s) {
+    if (!c) return TTN_ERR_ARG;
+    c->stream = (cudaStream_t)s;
+    return TTN_OK;
+}
+
+ttn_status ttn_set_precision(ttn_ctx* c, ttn_precision p) {
+    if (!c || (p != TTN_FP64 && p != TTN_SPLIT_TF32X3)) return TTN_ERR_ARG;
+    c->prec = p;
+    return TTN_OK;
+}
+
+ttn_status ttn_set_hamiltonian(ttn_ctx* c, const double* xy, double C6, double r_cut) {
+    if (!c || !xy || !std::isfinite(C6) || !std::isfinite(r_cut)) return TTN_ERR_ARG;
+    for (int i = 0; i < 2 * c->N; ++i)
+        if (!std::isfinite(xy[i])) return TTN_ERR_ARG;
+    for (int i = 0; i < c->N; ++i)
+        for (int j = i + 1; j < c->N; ++j)
+            if (xy[2 * i] == xy[2 * j] && xy[2 * i + 1] == xy[2 * j + 1]) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        c->xy.assign(xy, xy + 2 * c->N);
+        c->C6 = C6;
+        c->r_cut = r_cut;
+        set_V(c);
+        rebuild_up_envs(c);
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_apply_pulse(ttn_ctx* c, const ttn_pulse* sched, int n) {
+    if (!c || n < 0 || (n > 0 && !sched)) return TTN_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        const ttn_pulse& p = sched[i];
+        if (p.atom < 0 || p.atom >= c->N || !(p.t1 >= p.t0) || !std::isfinite(p.omega_x) ||
+            !std::isfinite(p.omega_z) || !std::isfinite(p.omega_r) || !std::isfinite(p.phase_r) ||
+            !std::isfinite(p.delta))
+            return TTN_ERR_ARG;
+    }
+    return guard(c, [&] {
+        std::vector<int> old = c->driven;
+        c->schedule.assign(sched, sched + n);
+        set_driven(c);
+        if (old != c->driven) {
+            centre_to_root(c);
+            set_phys_envs(c);
+            rebuild_up_envs(c);
+        }
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_set_product_state(ttn_ctx* c, const double* amps) {
+    if (!c || !amps) return TTN_ERR_ARG;
+    for (int i = 0; i < 6 * c->N; ++i)
+        if (!std::isfinite(amps[i])) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        std::vector<std::vector<zc>> lb(c->n_leaves);
+        for (int l = 0; l < c->n_leaves; ++l) {
+            int a = c->leaf_atom[l];
+            if (a < 0) lb[l] = {1.0, 0.0, 0.0};
+            else lb[l] = {zc(amps[6 * a], amps[6 * a + 1]), zc(amps[6 * a + 2], amps[6 * a + 3]),
+                          zc(amps[6 * a + 4], amps[6 * a + 5])};
+        }
+        build_from_branches(c, lb, 1, {zc(1.0)});
+        c->t = 0.0;
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_set_ghz_target(ttn_ctx* c, const int* mask, double phase) {
+    if (!c || !mask || !std::isfinite(phase)) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        std::vector<std::vector<zc>> lb(c->n_leaves);
+        for (int l = 0; l < c->n_leaves; ++l) {
+            int a = c->leaf_atom[l];
+            // column-major 3 x 2: branch 0 = |0>, branch 1 = |1> on mask atoms
+            std::vector<zc> m(6, zc(0.0));
+            m[0] = 1.0;
+            if (a >= 0 && mask[a]) m[3 + 1] = 1.0;
+            else m[3 + 0] = 1.0;
+            lb[l] = m;
+        }
+        double r = 1.0 / std::sqrt(2.0);
+        build_from_branches(c, lb, 2, {zc(r), std::polar(r, phase)});
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_tdvp_step(ttn_ctx* c, double dt) {
+    if (!c || !(dt > 0.0) || !std::isfinite(dt)) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        compute_coef(c, c->t + 0.5 * dt);
+        sweep_fwd(c, c->root, 0.5 * dt);
+        sweep_rev(c, c->root, 0.5 * dt);
+        c->t += dt;
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_overlap(ttn_ctx* c, const ttn_ctx* tgt, double* re_im) {
+    if (!c || !tgt || !re_im || tgt->Lx != c->Lx || tgt->Ly != c->Ly) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        if (tgt->centre != tgt->root) throw TtnError(TTN_ERR_STATE, "target centre is not at its root");
+        if (tgt->stream != c->stream) CUDA_OK(cudaStreamSynchronize(tgt->stream));
+        zc o = overlap(c, tgt);
+        re_im[0] = o.real();
+        re_im[1] = o.imag();
+    });
+}
+
+ttn_status ttn_fidelity(ttn_ctx* c, const ttn_ctx* tgt, double* F) {
+    if (!F) return TTN_ERR_ARG;
+    double o[2];
+    ttn_status st = ttn_overlap(c, tgt, o);
+    if (st == TTN_OK) *F = o[0] * o[0] + o[1] * o[1];
+    return st;
+}
+
+ttn_status ttn_measure(ttn_ctx* c, int which, double* out) {
+    if (!c || !out || which < 0 || which > 2) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        std::vector<double> v;
+        if (which == 2) {
+            // n stacks are kept in the environments of the root's children
+            const Env& e0 = env_of(c, c->root, 0);
+            const Env& e1 = env_of(c, c->root, 1);
+            std::vector<zc> vals;
+            root_expect(c, e0.nops, (int)e0.sites.size(), e1.nops, (int)e1.sites.size(), vals);
+            v.assign(c->N, 0.0);
+            size_t i = 0;
+            for (int a : e0.sites) v[a] = vals[i++].real();
+            for (int a : e1.sites) v[a] = vals[i++].real();
+        } else {
+            measure_projector(c, which, v);
+        }
+        std::copy(v.begin(), v.end(), out);
+    });
+}
+
+ttn_status ttn_norm(ttn_ctx* c, double* out) {
+    if (!c || !out) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        *out = root_norm(c);
+    });
+}
+
+ttn_status ttn_energy(ttn_ctx* c, double* out) {
+    if (!c || !out) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        *out = energy(c);
+    });
+}
+
+ttn_status ttn_get_time(ttn_ctx* c, double* t) {
+    if (!c || !t) return TTN_ERR_ARG;
+    *t = c->t;
+    return TTN_OK;
+}
+
+ttn_status ttn_get_dense(ttn_ctx* c, double* psi) {
+    if (!c || !psi || c->N > 9) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        sync_check(c);
+        int nn = (int)c->nodes.size();
+        // per node: vector over its leaves (leaf order, first fastest) x D
+        std::vector<std::vector<zc>> vec(nn);
+        std::vector<std::vector<int>> leaves(nn);
+        for (auto& lev : c->level_nodes)
+            for (int k : lev) {
+                const Node& nd = c->nodes[k];
+                std::vector<zc> X(nd.s);
+                CUDA_OK(cudaMemcpy(X.data(), c->T[k], sizeof(cplx) * nd.s, cudaMemcpyDeviceToHost));
+                std::vector<zc> part[2];
+                long long dimL[2];
+                for (int u = 0; u < 2; ++u) {
+                    int ch = nd.child[u];
+                    if (ch < 0) {
+                        part[u].assign(9, zc(0.0));
+                        for (int i = 0; i < 3; ++i) part[u][i + 3 * i] = 1.0;
+                        dimL[u] = 3;
+                        leaves[k].push_back(-ch - 1);
+                    } else {
+                        part[u] = vec[ch];
+                        dimL[u] = (long long)part[u].size() / nd.d[u];
+                        leaves[k].insert(leaves[k].end(), leaves[ch].begin(), leaves[ch].end());
+                    }
+                }
+                long long L0 = dimL[0], L1 = dimL[1];
+                int D = nd.d[2];
+                std::vector<zc> out(L0 * L1 * D, zc(0.0));
+                for (int cc = 0; cc < D; ++cc)
+                    for (int b = 0; b < nd.d[1]; ++b)
+                        for (int a = 0; a < nd.d[0]; ++a) {
+                            zc x = X[a + nd.d[0] * (b + (long long)nd.d[1] * cc)];
+                            if (x == zc(0.0)) continue;
+                            for (long long j = 0; j < L1; ++j) {
+                                zc y = x * part[1][j + L1 * b];
+                                if (y == zc(0.0)) continue;
+                                for (long long i = 0; i < L0; ++i)
+                                    out[i + L0 * (j + L1 * cc)] += part[0][i + L0 * a] * y;
+                            }
+                        }
+                vec[k] = out;
+            }
+        const std::vector<zc>& R = vec[c->root];
+        const std::vector<int>& lv = leaves[c->root];
+        long long dim = 1;
+        for (int i = 0; i < c->N; ++i) dim *= 3;
+        std::fill(psi, psi + 2 * dim, 0.0);
+        long long total = (long long)R.size();
+        for (long long e = 0; e < total; ++e) {
+            long long r = e, idx = 0;
+            bool ok = true;
+            for (size_t q = 0; q < lv.size(); ++q) {
+                int lvl = (int)(r % 3);
+                r /= 3;
+                int a = c->leaf_atom[lv[q]];
+                if (a < 0) {
+                    if (lvl != 0) ok = false;
+                    continue;
+                }
+                long long p3 = 1;
+                for (int i = 0; i < a; ++i) p3 *= 3;
+                idx += lvl * p3;
+            }
+            if (!ok) continue;
+            psi[2 * idx] += R[e].real();
+            psi[2 * idx + 1] += R[e].imag();
+        }
+    });
+}
+
+ttn_status ttn_save(ttn_ctx* c, const char* path) {
+    if (!c || !path) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        sync_check(c);
+        FILE* f = fopen(path, "wb");
+        if (!f) throw TtnError(TTN_ERR_ARG, "cannot open file");
+        int hdr[4] = {c->Lx, c->Ly, c->chi, (int)c->nodes.size()};
+        fwrite("TTN1", 1, 4, f);
+        fwrite(hdr, sizeof(int), 4, f);
+        fwrite(&c->t, sizeof(double), 1, f);
+        for (int k = 0; k < (int)c->nodes.size(); ++k) {
+            std::vector<cplx> X(c->nodes[k].s);
+            CUDA_OK(cudaMemcpy(X.data(), c->T[k], sizeof(cplx) * X.size(), cudaMemcpyDeviceToHost));
+            fwrite(X.data(), sizeof(cplx), X.size(), f);
+        }
+        fclose(f);
+    });
+}
+
+ttn_status ttn_load(ttn_ctx* c, const char* path) {
+    if (!c || !path) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        FILE* f = fopen(path, "rb");
+        if (!f) throw TtnError(TTN_ERR_ARG, "cannot open file");
+        char magic[4];
+        int hdr[4];
+        double t;
+        bool ok = fread(magic, 1, 4, f) == 4 && std::memcmp(magic, "TTN1", 4) == 0 &&
+                  fread(hdr, sizeof(int), 4, f) == 4 && fread(&t, sizeof(double), 1, f) == 1 &&
+                  hdr[0] == c->Lx && hdr[1] == c->Ly && hdr[2] == c->chi && hdr[3] == (int)c->nodes.size();
+        std::vector<std::vector<cplx>> data;
+        for (int k = 0; ok && k < (int)c->nodes.size(); ++k) {
+            std::vector<cplx> X(c->nodes[k].s);
+            ok = fread(X.data(), sizeof(cplx), X.size(), f) == X.size();
+            data.push_back(X);
+        }
+        fclose(f);
+        if (!ok) throw TtnError(TTN_ERR_ARG, "file does not match this context");
+        for (int k = 0; k < (int)c->nodes.size(); ++k)
+            CUDA_OK(cudaMemcpy(c->T[k], data[k].data(), sizeof(cplx) * data[k].size(), cudaMemcpyHostToDevice));
+        c->t = t;
+        c->centre = c->root;
+        rebuild_up_envs(c);
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_num_nodes(const ttn_ctx* c, int* n) {
+    if (!c || !n) return TTN_ERR_ARG;
+    *n = (int)c->nodes.size();
+    return TTN_OK;
+}
+
+ttn_status ttn_node_info(const ttn_ctx* c, int k, int* dims, int* children) {
+    if (!c || k < 0 || k >= (int)c->nodes.size()) return TTN_ERR_ARG;
+    for (int u = 0; u < 3; ++u)
+        if (dims) dims[u] = c->nodes[k].d[u];
+    for (int u = 0; u < 2; ++u)
+        if (children) children[u] = c->nodes[k].child[u];
+    return TTN_OK;
+}
+
+ttn_status ttn_leaf_atoms(const ttn_ctx* c, int* la, int* n) {
+    if (!c || !n) return TTN_ERR_ARG;
+    if (la) std::copy(c->leaf_atom.begin(), c->leaf_atom.end(), la);
+    *n = c->n_leaves;
+    return TTN_OK;
+}
+
+ttn_status ttn_get_node(ttn_ctx* c, int k, double* data) {
+    if (!c || !data || k < 0 || k >= (int)c->nodes.size()) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        CUDA_OK(cudaMemcpyAsync(data, c->T[k], sizeof(cplx) * c->nodes[k].s, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OK(cudaStreamSynchronize(c->stream));
+    });
+}
+
+ttn_status ttn_set_node(ttn_ctx* c, int k, const double* data) {
+    if (!c || !data || k < 0 || k >= (int)c->nodes.size()) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        CUDA_OK(cudaMemcpyAsync(c->T[k], data, sizeof(cplx) * c->nodes[k].s, cudaMemcpyHostToDevice, c->stream));
+        CUDA_OK(cudaStreamSynchronize(c->stream));
+        c->centre = c->root;
+    });
+}
+
+ttn_status ttn_refresh_envs(ttn_ctx* c) {
+    if (!c) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        c->centre = c->root;
+        rebuild_up_envs(c);
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_apply_heff(ttn_ctx* c, int k, const double* x, double* y) {
+    if (!c || !x || !y || k < 0 || k >= (int)c->nodes.size()) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        centre_to_root(c);
+        centre_to(c, k);
+        compute_coef(c, c->t);
+        const Node& nd = c->nodes[k];
+        CUDA_OK(cudaMemcpyAsync(c->tmp[1], x, sizeof(cplx) * nd.s, cudaMemcpyHostToDevice, c->stream));
+        const Env* e[3] = {&env_of(c, k, 0), &env_of(c, k, 1), &env_of(c, k, 2)};
+        cplx* hbs[3] = {nullptr, nullptr, nullptr};
+        int Dl[3] = {nd.d[0], nd.d[1], nd.d[2]};
+        for (int u = 0; u < 3; ++u)
+            if (env_has_block(*e[u])) {
+                assemble(c, *e[u], c->hb[u]);
+                hbs[u] = c->hb[u];
+            }
+        Pair pairs[3];
+        int np = setup_pairs(c, e, pairs);
+        heff_apply(c, nd.d, hbs, Dl, pairs, np, c->tmp[1], c->tmp[2]);
+        CUDA_OK(cudaMemcpyAsync(y, c->tmp[2], sizeof(cplx) * nd.s, cudaMemcpyDeviceToHost, c->stream));
+        sync_check(c);
+    });
+}
+
+ttn_status ttn_get_stats(const ttn_ctx* c, int64_t* out) {
+    if (!c || !out) return TTN_ERR_ARG;
+    for (int i = 0; i < 6; ++i) out[i] = c->stats[i];
+    std::memcpy(&out[2], &c->max_err, sizeof(double));
+    return TTN_OK;
+}
+
+ttn_status ttn_reset_stats(ttn_ctx* c) {
+    if (!c) return TTN_ERR_ARG;
+    for (int i = 0; i < 6; ++i) c->stats[i] = 0;
+    c->max_err = 0.0;
+    return TTN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+"""ctypes binding of libttn (include/ttn.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts NumPy
+arrays to pointers and status codes to exceptions.  There is no fallback: if
+the shared library is missing, importing it raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .workloads import PULSE_DTYPE
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libttn.so")
+
+STATUS = {0: "TTN_OK", 1: "TTN_ERR_ARG", 2: "TTN_ERR_ALLOC", 3: "TTN_ERR_CUDA", 4: "TTN_ERR_KRYLOV",
+          5: "TTN_ERR_NUMERIC", 6: "TTN_ERR_TIMEOUT", 7: "TTN_ERR_STATE"}
+FP64, SPLIT_TF32X3 = 0, 1
+
+# (name, restype, argtypes) for every symbol declared in include/ttn.h
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = [
+    ("ttn_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    ("ttn_destroy", None, [_P]),
+    ("ttn_last_error", ctypes.c_char_p, [_P]),
+    ("ttn_set_stream", ctypes.c_int, [_P, _P]),
+    ("ttn_set_precision", ctypes.c_int, [_P, ctypes.c_int]),
+    ("ttn_set_hamiltonian", ctypes.c_int, [_P, _D, ctypes.c_double, ctypes.c_double]),
+    ("ttn_apply_pulse", ctypes.c_int, [_P, _P, ctypes.c_int]),
+    ("ttn_set_product_state", ctypes.c_int, [_P, _D]),
+    ("ttn_set_ghz_target", ctypes.c_int, [_P, _I, ctypes.c_double]),
+    ("ttn_tdvp_step", ctypes.c_int, [_P, ctypes.c_double]),
+    ("ttn_fidelity", ctypes.c_int, [_P, _P, _D]),
+    ("ttn_overlap", ctypes.c_int, [_P, _P, _D]),
+    ("ttn_measure", ctypes.c_int, [_P, ctypes.c_int, _D]),
+    ("ttn_norm", ctypes.c_int, [_P, _D]),
+    ("ttn_energy", ctypes.c_int, [_P, _D]),
+    ("ttn_get_time", ctypes.c_int, [_P, _D]),
+    ("ttn_get_dense", ctypes.c_int, [_P, _D]),
+    ("ttn_save", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("ttn_load", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("ttn_num_nodes", ctypes.c_int, [_P, _I]),
+    ("ttn_node_info", ctypes.c_int, [_P, ctypes.c_int, _I, _I]),
+    ("ttn_leaf_atoms", ctypes.c_int, [_P, _I, _I]),
+    ("ttn_get_node", ctypes.c_int, [_P, ctypes.c_int, _D]),
+    ("ttn_set_node", ctypes.c_int, [_P, ctypes.c_int, _D]),
+    ("ttn_refresh_envs", ctypes.c_int, [_P]),
+    ("ttn_apply_heff", ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
+    ("ttn_get_stats", ctypes.c_int, [_P, _I64]),
+    ("ttn_reset_stats", ctypes.c_int, [_P]),
+]
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libttn.so (build it first with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libttn.so not found at %s: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TTNError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+class TTN:
+    """One TTN state on the GPU (a ``ttn_ctx``)."""
+
+    def __init__(self, Lx, Ly, chi, levels=3):
+        self.lib = load()
+        h = _P()
+        st = self.lib.ttn_create(Lx, Ly, levels, chi, ctypes.byref(h))
+        if st != 0:
+            raise TTNError(st, "ttn_create(%d, %d, %d, %d)" % (Lx, Ly, levels, chi))
+        self.h = h
+        self.Lx, self.Ly, self.chi, self.N = Lx, Ly, chi, Lx * Ly
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ttn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.ttn_last_error(self.h)
+            raise TTNError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    # -- configuration -------------------------------------------------------
+    def set_stream(self, stream):
+        """``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.ttn_set_stream(self.h, _P(raw or 0)), "set_stream")
+
+    def set_precision(self, p):
+        self._check(self.lib.ttn_set_precision(self.h, int(p)), "set_precision")
+
+    def set_hamiltonian(self, xy, C6, r_cut=0.0):
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(self.N, 2)
+        self._check(self.lib.ttn_set_hamiltonian(self.h, _dptr(xy), float(C6), float(r_cut)),
+                    "set_hamiltonian")
+
+    def apply_pulse(self, schedule):
+        from .workloads import to_pulse_array
+        arr = schedule if (isinstance(schedule, np.ndarray) and schedule.dtype == PULSE_DTYPE) \
+            else to_pulse_array(schedule)
+        arr = np.ascontiguousarray(arr)
+        self._check(self.lib.ttn_apply_pulse(self.h, arr.ctypes.data_as(_P), len(arr)), "apply_pulse")
+
+    def set_product_state(self, amps):
+        a = np.ascontiguousarray(np.asarray(amps, dtype=np.complex128).reshape(self.N, 3))
+        self._check(self.lib.ttn_set_product_state(self.h, a.view(np.float64).ctypes.data_as(_D)),
+                    "set_product_state")
+
+    def set_ghz(self, mask, phase=0.0):
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.int32).reshape(self.N))
+        self._check(self.lib.ttn_set_ghz_target(self.h, m.ctypes.data_as(_I), float(phase)),
+                    "set_ghz_target")
+
+    # -- evolution and observables -------------------------------------------
+    def step(self, dt):
+        self._check(self.lib.ttn_tdvp_step(self.h, float(dt)), "tdvp_step")
+
+    def overlap(self, target):
+        out = np.zeros(2)
+        self._check(self.lib.ttn_overlap(self.h, target.h, _dptr(out)), "overlap")
+        return complex(out[0], out[1])
+
+    def fidelity(self, target):
+        out = np.zeros(1)
+        self._check(self.lib.ttn_fidelity(self.h, target.h, _dptr(out)), "fidelity")
+        return float(out[0])
+
+    def measure(self, which):
+        out = np.zeros(self.N)
+        self._check(self.lib.ttn_measure(self.h, int(which), _dptr(out)), "measure")
+        return out
+
+    def norm(self):
+        out = np.zeros(1)
+        self._check(self.lib.ttn_norm(self.h, _dptr(out)), "norm")
+        return float(out[0])
+
+    def energy(self):
+        out = np.zeros(1)
+        self._check(self.lib.ttn_energy(self.h, _dptr(out)), "energy")
+        return float(out[0])
+
+    def time(self):
+        out = np.zeros(1)
+        self._check(self.lib.ttn_get_time(self.h, _dptr(out)), "get_time")
+        return float(out[0])
+
+    def dense(self):
+        out = np.zeros(2 * 3 ** self.N)
+        self._check(self.lib.ttn_get_dense(self.h, _dptr(out)), "get_dense")
+        return out.view(np.complex128)
+
+    def save(self, path):
+        self._check(self.lib.ttn_save(self.h, str(path).encode()), "save")
+
+    def load(self, path):
+        self._check(self.lib.ttn_load(self.h, str(path).encode()), "load")
+
+    # -- introspection -------------------------------------------------------
+    def num_nodes(self):
+        n = ctypes.c_int()
+        self._check(self.lib.ttn_num_nodes(self.h, ctypes.byref(n)), "num_nodes")
+        return n.value
+
+    def node_info(self, k):
+        dims = (ctypes.c_int * 3)()
+        ch = (ctypes.c_int * 2)()
+        self._check(self.lib.ttn_node_info(self.h, k, dims, ch), "node_info")
+        return tuple(dims), tuple(ch)
+
+    def leaf_atoms(self):
+        n = ctypes.c_int()
+        self._check(self.lib.ttn_leaf_atoms(self.h, None, ctypes.byref(n)), "leaf_atoms")
+        arr = (ctypes.c_int * n.value)()
+        self._check(self.lib.ttn_leaf_atoms(self.h, arr, ctypes.byref(n)), "leaf_atoms")
+        return list(arr)
+
+    def get_node(self, k):
+        """Node tensor as a (d0, d1, d2) complex array (same index meaning as
+        the oracle's tensors)."""
+        dims, _ = self.node_info(k)
+        buf = np.zeros(2 * dims[0] * dims[1] * dims[2])
+        self._check(self.lib.ttn_get_node(self.h, k, _dptr(buf)), "get_node")
+        return buf.view(np.complex128).reshape(dims, order="F")
+
+    def set_node(self, k, X):
+        dims, _ = self.node_info(k)
+        a = np.ascontiguousarray(np.asarray(X, dtype=np.complex128).reshape(dims).ravel(order="F"))
+        self._check(self.lib.ttn_set_node(self.h, k, a.view(np.float64).ctypes.data_as(_D)), "set_node")
+
+    def refresh_envs(self):
+        self._check(self.lib.ttn_refresh_envs(self.h), "refresh_envs")
+
+    def apply_heff(self, k, X):
+        dims, _ = self.node_info(k)
+        a = np.ascontiguousarray(np.asarray(X, dtype=np.complex128).reshape(dims).ravel(order="F"))
+        y = np.zeros(2 * a.size)
+        self._check(self.lib.ttn_apply_heff(self.h, k, a.view(np.float64).ctypes.data_as(_D), _dptr(y)),
+                    "apply_heff")
+        return y.view(np.complex128).reshape(dims, order="F")
+
+    def stats(self):
+        out = (ctypes.c_int64 * 6)()
+        self._check(self.lib.ttn_get_stats(self.h, out), "get_stats")
+        vals = list(out)
+        max_err = np.array([vals[2]], dtype=np.int64).view(np.float64)[0]
+        return {"krylov_runs": vals[0], "matvecs": vals[1], "max_krylov_err": float(max_err),
+                "launches": vals[3], "qr_calls": vals[4], "completed_columns": vals[5]}
+
+    def reset_stats(self):
+        self._check(self.lib.ttn_reset_stats(self.h), "reset_stats")

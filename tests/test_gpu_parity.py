@@ -1,0 +1,268 @@
+"""GPU (C-ABI) vs CPU oracle parity.  Tolerances:
+
+* exact regime (every bond at its full rank bound): the TTN must equal the
+  exact propagator, |1 - F| <= 1e-10 (FP64 tolerance of the fidelity target);
+* identical starting tensors: same algorithm, same deterministic QR
+  completion -> node tensors agree element by element to 1e-10 (round-off
+  times the conditioning of the QR; well-conditioned random inputs);
+* H_eff applied to a random tensor: element by element, relative 1e-12.
+"""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import exact, model, ttn as ottn
+from paper_2210_03763_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def native():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2210_03763_gb300 import native as nat
+    return nat
+
+
+def _pair(native, Lx, Ly, chi, C6=20.0, sched=None, amps=None, seed=0, r_cut=0.0):
+    N = Lx * Ly
+    xy = W.square_lattice(Lx, Ly)
+    if sched is None:
+        sched = W.random_constant_schedule(N, seed)
+    g = native.TTN(Lx, Ly, chi)
+    g.set_hamiltonian(xy, C6, r_cut)
+    g.apply_pulse(sched)
+    o = ottn.OracleTTN(Lx, Ly, chi, xy, C6, r_cut)
+    o.set_schedule(sched)
+    if amps is not None:
+        g.set_product_state(amps)
+        o.set_product_state(amps)
+    return g, o, xy, sched
+
+
+def _random_start(g, o, seed):
+    shapes = [o.tree.shape(k) for k in range(o.tree.n_nodes)]
+    Ts = W.random_ttn_tensors(shapes, seed)
+    for k, X in enumerate(Ts):
+        g.set_node(k, X)
+    g.refresh_envs()
+    o.set_tensors(Ts)
+
+
+def test_tree_matches_oracle(native):
+    for Lx, Ly, chi in ((2, 2, 16), (3, 3, 81), (4, 4, 64), (8, 8, 128), (5, 3, 7)):
+        from oracle.tree import Tree
+        g = native.TTN(Lx, Ly, chi)
+        tr = Tree(Lx, Ly, chi)
+        assert g.leaf_atoms() == tr.leaf_atom
+        assert g.num_nodes() == tr.n_nodes
+        for k in range(tr.n_nodes):
+            dims, ch = g.node_info(k)
+            assert dims == tr.shape(k)
+        g.close()
+
+
+@pytest.mark.parametrize("Lx,Ly,chi,steps", [(2, 2, 16, 5), (2, 3, 81, 3), (3, 3, 81, 2), (1, 3, 9, 4)])
+def test_exact_regime_equals_state_vector(native, Lx, Ly, chi, steps):
+    N = Lx * Ly
+    amps = W.random_product_amps(N, 3)
+    g, o, xy, sched = _pair(native, Lx, Ly, chi, amps=amps, seed=2)
+    V = model.pair_couplings(xy, 20.0)
+    psi = exact.product_state(amps)
+    assert np.linalg.norm(g.dense() - psi) < 1e-13
+    dt = 0.02
+    for s in range(steps):
+        g.step(dt)
+        psi = exact.step(psi, V, sched, s * dt, dt)
+    d = g.dense()
+    assert abs(1 - abs(np.vdot(psi, d)) ** 2) < 1e-10
+    assert np.allclose(g.measure(2), exact.expectation_local(psi, N, model.NR), atol=1e-10)
+    assert np.allclose(g.measure(0), exact.expectation_local(psi, N, model.P0), atol=1e-10)
+    assert np.allclose(g.measure(1), exact.expectation_local(psi, N, model.P1), atol=1e-10)
+    assert abs(g.energy() - exact.energy(psi, V, sched, g.time())) < 1e-9
+    g.close()
+
+
+def test_ghz_pulse_circuit_2x2(native):
+    # config-1 style: GHZ-4 from square and Jaksch pulses, exact 81-dim reference
+    xy = W.square_lattice(2, 2)
+    layers = W.schedule_layers(W.ghz_circuit(2, 2, root=0), xy, None)[:4]
+    sched, TL = W.layers_to_schedule(layers, 1.0)
+    g, o, _, _ = _pair(native, 2, 2, 16, sched=sched)
+    V = model.pair_couplings(xy, 20.0)
+    psi = exact.product_state(np.tile([1, 0, 0], (4, 1)))
+    dt = TL / 16
+    for s in range(len(layers) * 16):
+        g.step(dt)
+        psi = exact.step(psi, V, sched, s * dt, dt)
+    assert abs(1 - abs(np.vdot(psi, g.dense())) ** 2) < 1e-10
+    g.close()
+
+
+@pytest.mark.parametrize("start", ["random", "product"])
+def test_identical_start_same_trajectory(native, start):
+    # Truncated regime (4x4, chi = 12): same algorithm from the same tensors.
+    # From a random (full-rank) start every QR is unique and the tensors agree
+    # to round-off.  From a product state the bases are rank deficient: a
+    # column whose residual is just above the dependence threshold (1e-10
+    # ||A||) has its direction set by round-off amplified up to 1e-16/1e-10,
+    # so the gauge-dependent tensors agree to ~1e-6 while the state itself
+    # (gauge invariant) agrees to round-off.
+    Lx = Ly = 4
+    g, o, xy, sched = _pair(native, Lx, Ly, 12, seed=5)
+    if start == "random":
+        _random_start(g, o, 11)
+    else:
+        amps = W.random_product_amps(16, 4)
+        g.set_product_state(amps)
+        o.set_product_state(amps)
+        for k in range(o.tree.n_nodes):
+            assert np.allclose(g.get_node(k), o.T[k], atol=1e-12)
+    for _ in range(2):
+        g.step(0.03)
+        o.step(0.03)
+    tol_t = 1e-10 if start == "random" else 1e-4
+    for k in range(o.tree.n_nodes):
+        assert np.allclose(g.get_node(k), o.T[k], atol=tol_t), k
+    # the oracle's state loaded into a second GPU context: <oracle|gpu>
+    h = native.TTN(Lx, Ly, 12)
+    for k in range(o.tree.n_nodes):
+        h.set_node(k, o.T[k])
+    h.refresh_envs()
+    F = g.fidelity(h)
+    assert abs(1 - F / (g.norm() * o.norm())) < 1e-10
+    h.close()
+    assert abs(g.norm() - o.norm()) < 1e-12
+    assert abs(g.energy() - o.energy()) < 1e-10
+    assert np.allclose(g.measure(2), o.measure(2), atol=1e-11)
+    assert np.allclose(g.measure(0), o.measure(0), atol=1e-11)
+    g.close()
+
+
+def _oracle_centre_to(o, k):
+    tr = o.tree
+    path = []
+    x = k
+    while x != tr.root:
+        path.append(x)
+        x = tr.parent[x]
+    cur = tr.root
+    for ch in reversed(path):
+        u = 0 if tr.children[cur][0] == ("node", ch) else 1
+        o.T[cur], R = ottn.qr_leg(o.T[cur], u)
+        oth = [l for l in range(3) if l != u]
+        o.down[ch] = ottn.renormalize(o.T[cur], u, o.env(cur, oth[0]), o.env(cur, oth[1]), o.V)
+        o.T[ch] = ottn.apply_leg(R, o.T[ch], 2)
+        cur = ch
+
+
+@pytest.mark.parametrize("Lx,Ly,chi", [(4, 4, 16), (3, 3, 10)])
+def test_heff_elementwise(native, Lx, Ly, chi):
+    g, o, xy, sched = _pair(native, Lx, Ly, chi, seed=9)
+    _random_start(g, o, 21)
+    tr = o.tree
+    picks = [0, tr.level_nodes[1][0], tr.level_nodes[-2][-1], tr.root]
+    rng = np.random.default_rng(5)
+    for k in picks:
+        o.set_tensors([x.copy() for x in o.T])
+        shape = tr.shape(k)
+        X = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+        y_gpu = g.apply_heff(k, X)
+        _oracle_centre_to(o, k)
+        Hb, ch = o.heff_setup(k, o.coef(0.0))
+        y_ref = o.heff_apply(X, Hb, ch)
+        scale = np.max(abs(y_ref))
+        assert np.max(abs(y_gpu - y_ref)) <= 1e-12 * scale, k
+        # restore the canonical form of both sides
+        _random_start(g, o, 21)
+    g.close()
+
+
+def test_ghz_target_and_fidelity(native):
+    Lx, Ly = 3, 3
+    mask = [1, 1, 0, 1, 1, 1, 0, 1, 1]
+    t = native.TTN(Lx, Ly, 8)
+    t.set_ghz(mask, 0.3)
+    want = np.zeros(3 ** 9, complex)
+    want[0] = 1 / math.sqrt(2)
+    want[exact.basis_index(mask)] = np.exp(0.3j) / math.sqrt(2)
+    assert np.linalg.norm(t.dense() - want) < 1e-13
+    # fidelity of a product state with the GHZ target: |<GHZ|prod>|^2
+    amps = W.random_product_amps(9, 6)
+    p = native.TTN(Lx, Ly, 27)
+    p.set_product_state(amps)
+    f_ref = abs(np.vdot(want, exact.product_state(amps))) ** 2
+    assert abs(p.fidelity(t) - f_ref) < 1e-13
+    ov = p.overlap(t)
+    assert abs(ov - np.vdot(want, exact.product_state(amps))) < 1e-13
+    t.close()
+    p.close()
+
+
+def test_save_load_roundtrip(native):
+    g, o, _, _ = _pair(native, 3, 2, 9, amps=W.random_product_amps(6, 1), seed=3)
+    g.step(0.05)
+    d0 = g.dense()
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "s.ttn")
+        g.save(path)
+        h = native.TTN(3, 2, 9)
+        h.load(path)
+        assert np.allclose(h.dense(), d0, atol=1e-15)
+        assert abs(h.time() - 0.05) < 1e-15
+        bad = native.TTN(3, 2, 8)
+        with pytest.raises(native.TTNError):
+            bad.load(path)
+    g.close()
+
+
+def test_invalid_arguments_leave_state(native):
+    g = native.TTN(2, 2, 16)
+    amps = W.random_product_amps(4, 2)
+    g.set_product_state(amps)
+    d0 = g.dense()
+    xy = W.square_lattice(2, 2)
+    bad = xy.copy()
+    bad[1] = bad[0]
+    with pytest.raises(native.TTNError) as e:
+        g.set_hamiltonian(bad, 20.0)
+    assert e.value.code == 1
+    bad = xy.copy()
+    bad[2, 0] = np.nan
+    with pytest.raises(native.TTNError):
+        g.set_hamiltonian(bad, 20.0)
+    with pytest.raises(native.TTNError):
+        g.apply_pulse(np.array([[7, 0, 1, 1, 0, 0, 0, 0]]))   # atom out of range
+    with pytest.raises(native.TTNError):
+        g.step(-1.0)
+    with pytest.raises(native.TTNError):
+        g.measure(5)
+    assert np.allclose(g.dense(), d0)
+    g.close()
+
+
+def test_full_size_8x8_chi128_no_interaction_closed_form(native):
+    # 8x8, chi = 128 (the benchmark lattice and bond dimension), C6 = 0:
+    # the state stays a product of single-atom 3x3 exponentials.
+    N = 64
+    amps = W.random_product_amps(N, 12)
+    sched = W.random_constant_schedule(N, 13, atoms=range(0, 64, 8))
+    g, o, xy, _ = _pair(native, 8, 8, 128, C6=0.0, sched=sched, amps=amps)
+    dt = 0.05
+    g.step(dt)
+    ox, oz, w, de = model.coefficients(sched, N, 0.5 * dt)
+    from scipy.linalg import expm
+    states = np.array([expm(-1j * dt * model.local_term(ox[i], oz[i], w[i], de[i])) @ amps[i]
+                       for i in range(N)])
+    assert np.allclose(g.measure(2), abs(states[:, 2]) ** 2, atol=1e-12)
+    assert np.allclose(g.measure(1), abs(states[:, 1]) ** 2, atol=1e-12)
+    tgt = native.TTN(8, 8, 4)
+    tgt.set_product_state(states)
+    assert abs(g.fidelity(tgt) - 1) < 1e-11
+    g.close()
