@@ -169,6 +169,24 @@ ttn_status ttn_apply_heff(ttn_ctx* ctx, int node, const double* x, double* y);
  * matvecs, [2] max Krylov error estimate (as double bits), [3] kernel launches
  * issued by the library, [4] QR calls, [5] dependent columns completed. */
 ttn_status ttn_get_stats(const ttn_ctx* ctx, int64_t* out6);
+
+/* Kernel-level timing with CUDA events recorded on the context's stream.
+ * Between begin and end every contraction launch (and every QR) is bracketed
+ * by an event pair.  ttn_profile_end synchronises and fills out[16] with, for
+ * kind k = 0 tensor-core GEMM (tcgen05), 1 split-operand packing, 2 FP64
+ * GEMM, 3 QR: out[4k + 0] launches, [4k + 1] summed device time in ms,
+ * [4k + 2] algorithmic flops (8 M N K per complex contraction; 16 M D^2 per
+ * QR), [4k + 3] algorithmic bytes.  n must be >= 16. */
+ttn_status ttn_profile_begin(ttn_ctx* ctx);
+/* Self-test of one contraction kernel, no context needed: seeded random
+ * complex A (M x K) and B (K x N) with entries uniform in [-1, 1)^2
+ * (truncated to 11 significant bits when tf32_exact != 0, which isolates the
+ * accumulation error), C = A B by the FP64 kernel and by `precision`;
+ * *rel_err receives max|C_p - C_fp64| / max|C_fp64|.  Sizes above 2^26
+ * elements -> TTN_ERR_ARG. */
+ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned long long seed,
+                                 int tf32_exact, double* rel_err);
+ttn_status ttn_profile_end(ttn_ctx* ctx, double* out, int n);
 ttn_status ttn_reset_stats(ttn_ctx* ctx);
 
 #ifdef __cplusplus

@@ -22,11 +22,15 @@ struct GemmArgs {
 
 // Launch on `stream`; returns the number of kernels launched (0 if empty).
 int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream);
-// Split-precision tensor-core path (3xTF32 on tcgen05); falls back to nothing:
-// returns -1 when the shape is not supported so the caller can use FP64.
+// Split-precision tensor-core path (3xTF32 on tcgen05).  Returns kernels
+// launched, -1 when the shape is not handled there (too small: the caller
+// uses FP64), -2 when the workspace is smaller than split_workspace_bytes.
+// The workspace's first int is an error flag a timed-out wait sets.
 int launch_zgemm_split(const GemmArgs& g, cudaStream_t stream, void* workspace,
                        size_t workspace_bytes);
 size_t split_workspace_bytes(const GemmArgs& g);
+int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes);
+int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes);
 
 // ---- Lanczos / vector kernels (kernels.cu) --------------------------------
 // Fixed partial-sum grid for reductions: deterministic order, no atomics.
@@ -46,24 +50,21 @@ struct KrylovScalars {
     int    nonfinite;
 };
 
+int red_blocks_for(long long n);
 int k_norm2_partial(const cplx* x, long long n, double* partial, cudaStream_t s);
-int k_dots_partial(const cplx* V, long long ld, int nv, const cplx* w, long long n,
-                   cplx* partial, cudaStream_t s);
-int k_reduce_dots(const cplx* partial, int nv, cplx* out, cudaStream_t s);
-int k_reduce_norm(const double* partial, double* out, cudaStream_t s);
-// w -= sum_i V_i h_i; then (mode 1) partial dots of the new w with V_0..V_{nv-1},
-// or (mode 2) the partial norm^2 of the new w.
-int k_orth_update(const cplx* V, long long ld, int nv, const cplx* h, cplx* w, long long n,
-                  int mode, cplx* partial_dots, double* partial_norm, cudaStream_t s);
-int k_scale_copy(const cplx* x, long long n, const double* scale, int invert_sqrt,
-                 cplx* y, cudaStream_t s);
+int k_dots_scaled(cplx* V, long long ld, int nv, const cplx* w, long long n, cplx* partial, int scale_col,
+                  const double* scale_src, long long skip_col, cudaStream_t s);
+// h = fixed-order sum of partial_in; w -= sum_i V_i h_i; then mode 1: partial
+// dots of the new w with V_0..V_{nv-1}, mode 2: partial norm^2 of the new w.
+int k_orth_update_ex(const cplx* V, long long ld, int nv, const cplx* partial_in, cplx* w, long long n,
+                     int mode, cplx* partial_dots, double* partial_norm, cplx* h_out, int accumulate,
+                     long long skip_col, cudaStream_t s);
+int k_scale_copy_dev(const cplx* x, long long n, const double* scale, cplx* y, cudaStream_t s);
+int k_krylov_start_ex(KrylovScalars* ks, const double* nrm2_partial, long long n, cudaStream_t s);
+int k_krylov_scalars_ex(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial,
+                        long long n, int j, double zr, double zi, double tol, cudaStream_t s);
 int k_combine(const cplx* V, long long ld, int nv, const KrylovScalars* ks, cplx* y,
               long long n, cudaStream_t s);
-// Krylov step bookkeeping: alpha_j, beta_j, tridiagonal exponential, error.
-int k_krylov_scalars(KrylovScalars* ks, const cplx* h1, const cplx* h2,
-                     const double* beta2, int j, double z_re, double z_im,
-                     double tol, cudaStream_t s);
-int k_krylov_start(KrylovScalars* ks, const double* nrm2, cudaStream_t s);
 
 // ---- elementwise / assembly ---------------------------------------------------
 int k_permute3(const cplx* x, cplx* y, int d0, int d1, int d2, int p0, int p1, int p2,

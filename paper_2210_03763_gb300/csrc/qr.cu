@@ -15,13 +15,6 @@
 // [update, dots] -> [update, norm] -> [finish: R_kk, flag, 1/R_kk].
 #include "common.cuh"
 
-int red_blocks_for(long long n);
-int k_dots_scaled(cplx* V, long long ld, int nv, const cplx* w, long long n, cplx* partial, int scale_col,
-                  const double* scale_src, long long skip_col, cudaStream_t s);
-int k_orth_update_ex(const cplx* V, long long ld, int nv, const cplx* partial_in, cplx* w, long long n,
-                     int mode, cplx* partial_dots, double* partial_norm, cplx* h_out, int accumulate,
-                     long long skip_col, cudaStream_t s);
-
 namespace {
 
 constexpr double QR_TOL = 1e-10;

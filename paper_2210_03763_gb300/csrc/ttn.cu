@@ -22,17 +22,6 @@
 #include <string>
 #include <vector>
 
-int red_blocks_for(long long n);
-int k_dots_scaled(cplx* V, long long ld, int nv, const cplx* w, long long n, cplx* partial, int scale_col,
-                  const double* scale_src, long long skip_col, cudaStream_t s);
-int k_orth_update_ex(const cplx* V, long long ld, int nv, const cplx* partial_in, cplx* w, long long n,
-                     int mode, cplx* partial_dots, double* partial_norm, cplx* h_out, int accumulate,
-                     long long skip_col, cudaStream_t s);
-int k_scale_copy_dev(const cplx* x, long long n, const double* scale, cplx* y, cudaStream_t s);
-int k_krylov_start_ex(KrylovScalars* ks, const double* nrm2_partial, long long n, cudaStream_t s);
-int k_krylov_scalars_ex(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial,
-                        long long n, int j, double zr, double zi, double tol, cudaStream_t s);
-
 namespace {
 
 typedef std::complex<double> zc;
@@ -156,6 +145,14 @@ struct ttn_ctx {
     Env dummy;
     std::map<std::pair<const Env*, const Env*>, cplx*> vsub;   // G-stack GEMM operands
 
+    // kernel-level profile: event pairs around launches while enabled
+    bool profiling = false;
+    struct ProfRec { int kind; cudaEvent_t e0, e1; double flops, bytes; };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    void* split_ws = nullptr;   // packed operands of the split GEMM (+ error flag)
+    size_t split_cap = 0;
     int64_t stats[6] = {0, 0, 0, 0, 0, 0};
     double max_err = 0.0;
     std::vector<void*> allocs;
@@ -184,11 +181,106 @@ long long ipow3_capped(int k, long long cap) {
 int leg_dim(const ttn_ctx* c, int k, int leg) { return c->nodes[k].d[leg]; }
 
 // ------------------------------------------------------------------ GEMMs
+void grow_split_ws(ttn_ctx* c, size_t bytes) {
+    if (bytes <= c->split_cap) return;
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    int flag = 0;
+    if (c->split_ws) {
+        CUDA_OK(cudaMemcpy(&flag, c->split_ws, sizeof(int), cudaMemcpyDeviceToHost));
+        cudaFree(c->split_ws);
+        c->split_ws = nullptr;
+        c->split_cap = 0;
+    }
+    size_t cap = bytes + bytes / 4;
+    if (cudaMalloc(&c->split_ws, cap) != cudaSuccess) throw TtnError(TTN_ERR_ALLOC, "split workspace");
+    CUDA_OK(cudaMemcpy(c->split_ws, &flag, sizeof(int), cudaMemcpyHostToDevice));
+    c->split_cap = cap;
+}
+
+// Profile kinds: 0 tensor-core GEMM, 1 split packing, 2 FP64 GEMM, 3 QR.
+enum { PK_TC = 0, PK_PACK = 1, PK_F64 = 2, PK_QR = 3, PK_N = 4 };
+
+cudaEvent_t next_event(ttn_ctx* c) {
+    if (c->ev_next == c->ev_pool.size()) {
+        cudaEvent_t e;
+        CUDA_OK(cudaEventCreate(&e));
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_next++];
+}
+
+struct ProfScope {
+    ttn_ctx* c;
+    int kind;
+    double flops, bytes;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(ttn_ctx* c_, int k, double f = 0, double b = 0) : c(c_), kind(k), flops(f), bytes(b) {
+        if (c->profiling) {
+            e0 = next_event(c);
+            CUDA_OK(cudaEventRecord(e0, c->stream));
+        }
+    }
+    ~ProfScope() {
+        if (c->profiling && e0) {
+            cudaEvent_t e1 = next_event(c);
+            cudaEventRecord(e1, c->stream);
+            c->prof.push_back({kind, e0, e1, flops, bytes});
+        }
+    }
+};
+
+double gemm_flops(const GemmArgs& g) {
+    return 8.0 * g.M * (double)g.N * g.Ki * (double)g.Ko * g.Bi * (double)g.Bo;
+}
+
+// Contractions that write the state itself (absorbing a link matrix into a
+// node) and observables always run in FP64: the tensor core's FP32
+// accumulation rounds with a small bias (results shrink by ~1e-7 relative),
+// which in a state update is a norm loss that accumulates step after step,
+// while in an H_eff product or an environment it only perturbs the
+// generator (the Lanczos propagator stays unitary).
+thread_local bool g_force_fp64 = false;
+struct ForceFp64 {
+    bool old;
+    ForceFp64() : old(g_force_fp64) { g_force_fp64 = true; }
+    ~ForceFp64() { g_force_fp64 = old; }
+};
+
 void gemm(ttn_ctx* c, const GemmArgs& g) {
     int n = -1;
-    if (c->prec == TTN_SPLIT_TF32X3) n = launch_zgemm_split(g, c->stream, nullptr, 0);
-    if (n < 0) n = launch_zgemm_f64(g, c->stream);
+    const double fl = gemm_flops(g);
+    if (c->prec == TTN_SPLIT_TF32X3 && !g_force_fp64) {
+        size_t need = split_workspace_bytes(g);
+        if (need > 0) {
+            grow_split_ws(c, need);
+            double nb = (double)g.Bi * g.Bo;
+            double pack_bytes = nb * ((double)g.M + g.N) * g.Ki * (double)g.Ko * 16.0 + 0.5 * need;
+            {
+                ProfScope ps(c, PK_PACK, 0.0, pack_bytes);
+                n = launch_split_pack(g, c->stream, c->split_ws, c->split_cap);
+            }
+            if (n >= 0) {
+                ProfScope ps(c, PK_TC, fl, 0.5 * need + nb * (double)g.M * g.N * 16.0);
+                int m = launch_split_mma(g, c->stream, c->split_ws, c->split_cap);
+                if (m < 0) throw TtnError(TTN_ERR_CUDA, "split GEMM launch failed after packing");
+                n += m;
+            }
+        }
+    }
+    if (n < 0) {
+        ProfScope ps(c, PK_F64, fl, 0.0);
+        n = launch_zgemm_f64(g, c->stream);
+    }
     c->stats[3] += n;
+}
+
+// A bounded device-side wait of the split GEMM gave up -> TTN_ERR_TIMEOUT.
+void check_split_flag(ttn_ctx* c) {
+    if (!c->split_ws) return;
+    int flag = 0;
+    CUDA_OK(cudaMemcpyAsync(&flag, c->split_ws, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    if (flag) throw TtnError(TTN_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
 }
 
 GemmArgs base_args() {
@@ -531,7 +623,10 @@ void qr_leg(ttn_ctx* c, int k, int o) {
     }
     int ndep = 0;
     auto key = std::make_pair(k, o);
-    c->stats[3] += qr_cgs2(A, (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep);
+    {
+        ProfScope ps(c, PK_QR, 16.0 * (double)M * D * D, 0.0);
+        c->stats[3] += qr_cgs2(A, (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep);
+    }
     c->stats[4] += 1;
     c->stats[5] += ndep;
     if (o != 2)
@@ -539,8 +634,9 @@ void qr_leg(ttn_ctx* c, int k, int o) {
                                   PERM[o][2], 1, c->stream);
 }
 
-// node k <- Rbuf x_leg node k   (absorb the link matrix)
+// node k <- Rbuf x_leg node k   (absorb the link matrix; FP64, see gemm())
 void absorb(ttn_ctx* c, int k, int leg) {
+    ForceFp64 f64;
     const Node& nd = c->nodes[k];
     leg_apply(c, c->Rbuf, nd.d[leg], c->T[k], nd.d, leg, c->tmp[1], 0.0);
     std::swap(c->T[k], c->tmp[1]);
@@ -928,6 +1024,7 @@ void set_V(ttn_ctx* c) {
 // ------------------------------------------------------------- observables
 // <psi| op_i |psi> for ops renormalised to the root legs (centre at root).
 void root_expect(ttn_ctx* c, const cplx* st0, int n0, const cplx* st1, int n1, std::vector<zc>& out) {
+    ForceFp64 f64;
     const Node& nd = c->nodes[c->root];
     long long s = nd.s;
     out.assign(n0 + n1, zc(0.0));
@@ -953,6 +1050,7 @@ void root_expect(ttn_ctx* c, const cplx* st0, int n0, const cplx* st1, int n1, s
 }
 
 double root_norm(ttn_ctx* c) {
+    ForceFp64 f64;
     const Node& nd = c->nodes[c->root];
     project(c, c->T[c->root], nd.d, c->T[c->root], nd.d, 2, c->Gbuf[2], 1, 0, 0);
     cplx h;
@@ -963,6 +1061,7 @@ double root_norm(ttn_ctx* c) {
 
 // Renormalise one diagonal one-site operator (per atom) up to the root legs.
 void measure_projector(ttn_ctx* c, int level_index, std::vector<double>& out) {
+    ForceFp64 f64;
     // bare operator: |level><level|
     cplx bare[9];
     for (int i = 0; i < 9; ++i) bare[i] = C(0.0);
@@ -1024,6 +1123,7 @@ void measure_projector(ttn_ctx* c, int level_index, std::vector<double>& out) {
 }
 
 zc overlap(ttn_ctx* psi, const ttn_ctx* tgt) {
+    ForceFp64 f64;
     ttn_ctx* c = psi;
     int nn = (int)c->nodes.size();
     std::vector<cplx*> M(nn, nullptr);
@@ -1059,6 +1159,7 @@ zc overlap(ttn_ctx* psi, const ttn_ctx* tgt) {
 }
 
 double energy(ttn_ctx* c) {
+    ForceFp64 f64;
     compute_coef(c, c->t);
     int k = c->root;
     const Node& nd = c->nodes[k];
@@ -1083,6 +1184,7 @@ double energy(ttn_ctx* c) {
 void sync_check(ttn_ctx* c) {
     CUDA_OK(cudaStreamSynchronize(c->stream));
     CUDA_OK(cudaGetLastError());
+    check_split_flag(c);
 }
 
 template <class F>
@@ -1142,7 +1244,10 @@ ttn_status ttn_create(int Lx, int Ly, int levels, int chi, ttn_ctx** out) {
 
 void ttn_destroy(ttn_ctx* c) {
     if (!c) return;
+    cudaStreamSynchronize(c->stream);
     for (void* p : c->allocs) cudaFree(p);
+    if (c->split_ws) cudaFree(c->split_ws);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->hflag) cudaFreeHost(c->hflag);
     delete c;
 }
@@ -1505,6 +1610,94 @@ ttn_status ttn_apply_heff(ttn_ctx* c, int k, const double* x, double* y) {
         heff_apply(c, nd.d, hbs, Dl, pairs, np, c->tmp[1], c->tmp[2]);
         CUDA_OK(cudaMemcpyAsync(y, c->tmp[2], sizeof(cplx) * nd.s, cudaMemcpyDeviceToHost, c->stream));
         sync_check(c);
+    });
+}
+
+ttn_status ttn_profile_begin(ttn_ctx* c) {
+    if (!c) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        CUDA_OK(cudaStreamSynchronize(c->stream));
+        c->prof.clear();
+        c->ev_next = 0;
+        c->profiling = true;
+    });
+}
+
+ttn_status ttn_profile_end(ttn_ctx* c, double* out, int n) {
+    if (!c || !out || n < 4 * PK_N) return TTN_ERR_ARG;
+    return guard(c, [&] {
+        c->profiling = false;
+        CUDA_OK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < 4 * PK_N; ++i) out[i] = 0.0;
+        for (auto& r : c->prof) {
+            float ms = 0.f;
+            CUDA_OK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+            out[4 * r.kind + 0] += 1.0;
+            out[4 * r.kind + 1] += ms;
+            out[4 * r.kind + 2] += r.flops;
+            out[4 * r.kind + 3] += r.bytes;
+        }
+        c->prof.clear();
+        c->ev_next = 0;
+    });
+}
+
+// Random (seeded, uniform in [-1, 1)) complex operands, C = A B with A M x K
+// and B K x N column-major, in FP64 and in the chosen precision.
+__global__ void selftest_fill(cplx* x, long long n, unsigned long long seed, int tf32_exact) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(e + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        double re = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+        z = z * 0x2545F4914F6CDD1DULL + 1;
+        z ^= z >> 29;
+        double im = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+        if (tf32_exact) {   // keep 11 significant bits: exactly representable in TF32
+            re = (double)__uint_as_float(__float_as_uint((float)re) & 0xFFFFE000u);
+            im = (double)__uint_as_float(__float_as_uint((float)im) & 0xFFFFE000u);
+        }
+        x[e] = make_double2(re, im);
+    }
+}
+
+ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned long long seed, int tf32_exact,
+                                 double* rel_err) {
+    if (M < 1 || N < 1 || K < 1 || !rel_err || (long long)M * N > (1LL << 26) || (long long)M * K > (1LL << 26) ||
+        (long long)K * N > (1LL << 26))
+        return TTN_ERR_ARG;
+    ttn_ctx tmp;
+    tmp.prec = (ttn_precision)precision;
+    return guard(&tmp, [&] {
+        cplx *A = (cplx*)dalloc(&tmp, sizeof(cplx) * M * K), *B = (cplx*)dalloc(&tmp, sizeof(cplx) * K * N);
+        cplx *C0 = (cplx*)dalloc(&tmp, sizeof(cplx) * M * N), *C1 = (cplx*)dalloc(&tmp, sizeof(cplx) * M * N);
+        selftest_fill<<<256, 256>>>(A, (long long)M * K, seed, tf32_exact);
+        selftest_fill<<<256, 256>>>(B, (long long)K * N, seed * 31 + 7, tf32_exact);
+        GemmArgs g = base_args();
+        g.M = M; g.N = N; g.Ki = K;
+        g.A = A; g.a_m = 1; g.a_ki = M;
+        g.B = B; g.b_ki = 1; g.b_n = K;
+        g.C = C0; g.c_m = 1; g.c_n = M;
+        launch_zgemm_f64(g, nullptr);
+        g.C = C1;
+        tmp.stream = nullptr;
+        gemm(&tmp, g);
+        CUDA_OK(cudaDeviceSynchronize());
+        std::vector<cplx> h0((size_t)M * N), h1((size_t)M * N);
+        CUDA_OK(cudaMemcpy(h0.data(), C0, sizeof(cplx) * h0.size(), cudaMemcpyDeviceToHost));
+        CUDA_OK(cudaMemcpy(h1.data(), C1, sizeof(cplx) * h1.size(), cudaMemcpyDeviceToHost));
+        double mx = 0.0, me = 0.0;
+        for (size_t i = 0; i < h0.size(); ++i) {
+            mx = std::max(mx, std::hypot(h0[i].x, h0[i].y));
+            me = std::max(me, std::hypot(h1[i].x - h0[i].x, h1[i].y - h0[i].y));
+        }
+        *rel_err = mx > 0 ? me / mx : me;
+        for (void* p : tmp.allocs) cudaFree(p);
+        tmp.allocs.clear();
+        if (tmp.split_ws) cudaFree(tmp.split_ws);
+        tmp.split_ws = nullptr;
     });
 }
 

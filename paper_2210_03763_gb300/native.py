@@ -51,6 +51,10 @@ SIGNATURES = [
     ("ttn_refresh_envs", ctypes.c_int, [_P]),
     ("ttn_apply_heff", ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
     ("ttn_get_stats", ctypes.c_int, [_P, _I64]),
+    ("ttn_profile_begin", ctypes.c_int, [_P]),
+    ("ttn_selftest_contract", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_ulonglong, ctypes.c_int, _D]),
+    ("ttn_profile_end", ctypes.c_int, [_P, _D, ctypes.c_int]),
     ("ttn_reset_stats", ctypes.c_int, [_P]),
 ]
 
@@ -72,6 +76,16 @@ def load(path=LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def selftest_contract(M, N, K, precision, seed=1, tf32_exact=False):
+    """max|C_p - C_fp64| / max|C_fp64| for one random M x K x N contraction."""
+    lib = load()
+    out = np.zeros(1)
+    st = lib.ttn_selftest_contract(M, N, K, int(precision), seed, int(tf32_exact), _dptr(out))
+    if st != 0:
+        raise TTNError(st, "selftest_contract")
+    return float(out[0])
 
 
 class TTNError(RuntimeError):
@@ -238,6 +252,17 @@ class TTN:
         max_err = np.array([vals[2]], dtype=np.int64).view(np.float64)[0]
         return {"krylov_runs": vals[0], "matvecs": vals[1], "max_krylov_err": float(max_err),
                 "launches": vals[3], "qr_calls": vals[4], "completed_columns": vals[5]}
+
+    PROFILE_KINDS = ("tc_gemm", "split_pack", "f64_gemm", "qr")
+
+    def profile_begin(self):
+        self._check(self.lib.ttn_profile_begin(self.h), "profile_begin")
+
+    def profile_end(self):
+        out = np.zeros(16)
+        self._check(self.lib.ttn_profile_end(self.h, _dptr(out), 16), "profile_end")
+        return {k: {"launches": int(out[4 * i]), "ms": out[4 * i + 1], "flops": out[4 * i + 2],
+                    "bytes": out[4 * i + 3]} for i, k in enumerate(self.PROFILE_KINDS)}
 
     def reset_stats(self):
         self._check(self.lib.ttn_reset_stats(self.h), "reset_stats")
