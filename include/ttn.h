@@ -189,6 +189,34 @@ ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned lo
 ttn_status ttn_profile_end(ttn_ctx* ctx, double* out, int n);
 ttn_status ttn_reset_stats(ttn_ctx* ctx);
 
+/* ---- allocation-free contraction ----------------------------------------
+ * The paper has no counterpart to this call: it serves callers that cannot
+ * allocate device memory at the point of the call (a host program whose
+ * memory is owned by its own pool or a fixed budget, or code that must not
+ * call cudaMalloc/cudaFree because they synchronise the device).
+ *
+ * C = A B for complex matrices in device memory, column-major, interleaved
+ * (re, im) doubles: A is M x K (lda = M), B is K x N (ldb = K), C is M x N
+ * (ldc = M), caller-allocated; C is overwritten.  It runs the split-precision
+ * tensor-core contraction (3xTF32, ~5e-7 of max|C|) when the shape fills the
+ * tensor-core tiles, else the FP64 kernel, on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream), and returns without synchronising.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  The packed
+ * operands live in one file-scope device array of 8 MiB, which every GPU that
+ * loads this library holds until the process exits; a shape whose packed
+ * operands need more (about 2 * (round_up(2 min(M,N), 128) + round_up(
+ * max(M,N), 64)) * round_up(2K, 32) * 4 bytes) returns TTN_ERR_ARG and does
+ * nothing.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call shares the one array and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Errors: TTN_ERR_ARG for null pointers, non-positive or too large sizes;
+ * TTN_ERR_CUDA if a launch fails. */
+ttn_status ttn_contract_split_noalloc(const double* A, const double* B, double* C, int M, int N, int K,
+                                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,7 @@ SIGNATURES = [
                                              ctypes.c_ulonglong, ctypes.c_int, _D]),
     ("ttn_profile_end", ctypes.c_int, [_P, _D, ctypes.c_int]),
     ("ttn_reset_stats", ctypes.c_int, [_P]),
+    ("ttn_contract_split_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
 ]
 
 _lib = None
@@ -86,6 +87,16 @@ def selftest_contract(M, N, K, precision, seed=1, tf32_exact=False):
     if st != 0:
         raise TTNError(st, "selftest_contract")
     return float(out[0])
+
+
+def contract_split_noalloc(A_ptr, B_ptr, C_ptr, M, N, K, stream=None):
+    """C = A B on device buffers (column-major complex128) without allocating;
+    pointers are raw device addresses (e.g. torch tensor.data_ptr())."""
+    lib = load()
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib.ttn_contract_split_noalloc(_P(A_ptr), _P(B_ptr), _P(C_ptr), M, N, K, _P(raw or 0))
+    if st != 0:
+        raise TTNError(st, "contract_split_noalloc(%d, %d, %d)" % (M, N, K))
 
 
 class TTNError(RuntimeError):
