@@ -187,6 +187,11 @@ ttn_status ttn_profile_begin(ttn_ctx* ctx);
 ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned long long seed,
                                  int tf32_exact, double* rel_err);
 ttn_status ttn_profile_end(ttn_ctx* ctx, double* out, int n);
+/* Per-launch records of the last profile: 7 doubles each (kind, M, N, K,
+ * batches, ms, algorithmic flops; K and batches are the products of the
+ * two-level extents).  *n_records receives the count; at most max_records
+ * are written to out (which may be NULL to query the count). */
+ttn_status ttn_profile_records(const ttn_ctx* ctx, double* out, int max_records, int* n_records);
 ttn_status ttn_reset_stats(ttn_ctx* ctx);
 
 /* ---- allocation-free contraction ----------------------------------------

@@ -77,6 +77,11 @@ int k_assemble_block(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsite
 int k_check_finite(const cplx* x, long long n, int* flag, cudaStream_t s);
 
 // ---- QR (qr.cu) ----------------------------------------------------------------
+// QR kernels use one block per QR_ROWS rows; partial sums are sized
+// G = ceil(M / QR_ROWS) per column (part: 2 * G * (D + 1) complex), and the
+// Frobenius pass uses up to QR_FROB_BLOCKS partials (pnorm >= max of both).
+constexpr int QR_ROWS = 128;
+constexpr int QR_FROB_BLOCKS = 1024;
 struct QrScratch {
     cplx* part;         // RED_BLOCKS * (D + 1) partial dots
     cplx* h;            // D + 1 projections
@@ -86,7 +91,16 @@ struct QrScratch {
     double* rownorm;    // M row norms of Q (completion)
     int* cand;          // candidate order (M)
     int* pick;          // chosen candidate
+    // structured completion
+    int* kept;          // D: kept column positions
+    int* dep;           // D: dependent column positions
+    int* acc_rows;      // D: accepted candidate row per completed column
+    cplx* Y;            // QR_SC_MAXR * D: coefficients y_t
+    double* nu;         // D: residual norms
+    int* row_rank;      // M: step at which a row was accepted (INT_MAX: never)
+    int* cand_used;     // M: candidate accepted flags
 };
+constexpr int QR_SC_MAXR = 64;   // structured completion when the kept rank r <= this
 // In-place QR of the column-major M x D matrix A (lda = M): A <- Q, R (D x D,
 // column-major) written.  cand[0..ncand) is the completion candidate order.
 int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand,

@@ -3,8 +3,9 @@
 // Every contraction of the TDVP update -- a matrix on one leg of a 3-leg node
 // tensor, the channel sums of the cross terms, the environment
 // renormalisations X^H (op x X) -- is one call of this kernel with suitable
-// strides.  Tile: 64 x 64 complex outputs per CTA, 256 threads, 4 x 4 complex
-// accumulators per thread, K staged through shared memory in slices of 8.
+// strides.  Tile: 64 or 16 complex outputs per side (picked from M and N),
+// 256 threads, up to 4 x 4 complex accumulators per thread, K staged through
+// shared memory in slices of 8.
 // GB300's FP64 pipe (about 2 DFMA/clk/SM) is the bound, not memory: a simple
 // register-tiled loop is enough to saturate it, so loads use generic strides
 // (with bounds checks that zero-fill) rather than TMA.
@@ -12,9 +13,8 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 8;
-constexpr int TM = 4, TN = 4;            // per-thread complex tile
-constexpr int THREADS = (BM / TM) * (BN / TN);
+constexpr int BK = 8;
+constexpr int THREADS = 256;   // 16 x 16 threads; each owns a TM x TN register tile
 
 __device__ __forceinline__ cplx cmul_acc(cplx acc, cplx a, cplx b) {
     acc.x = fma(a.x, b.x, acc.x);
@@ -24,7 +24,12 @@ __device__ __forceinline__ cplx cmul_acc(cplx acc, cplx a, cplx b) {
     return acc;
 }
 
+// Tile BM x BN (each 16 or 64), chosen from the problem shape so that small
+// outputs (3 x 3 physical legs, 9 x 9 projections) do not spend GB300's scarce
+// FP64 throughput on padding.
+template <int BM, int BN>
 __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
+    constexpr int TM = BM / 16, TN = BN / 16;
     __shared__ cplx As[2][BK][BM];
     __shared__ cplx Bs[2][BK][BN];
 
@@ -36,7 +41,9 @@ __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int K = g.Ki * g.Ko;
     const int tid = threadIdx.x;
-    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int tx = tid % 16, ty = tid / 16;
+    // warps whose rows (or columns) are all outside the matrix skip the FMAs
+    const bool active = (m0 + ty < g.M) && (n0 + tx < g.N);
 
     cplx acc[TM][TN];
 #pragma unroll
@@ -44,12 +51,9 @@ __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
-    // each thread stages 2 elements of the A slice and 2 of the B slice
     auto load = [&](int k0, int buf) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            int e = tid + r * THREADS;            // 0 .. BK*BM-1
-            int kk = e / BM, mm = e % BM;         // A: m fastest
+        for (int e = tid; e < BK * BM; e += THREADS) {
+            int kk = e / BM, mm = e % BM;          // A: m fastest
             int m = m0 + mm, k = k0 + kk;
             cplx v = make_double2(0.0, 0.0);
             if (m < g.M && k < K) {
@@ -58,7 +62,9 @@ __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
                 if (g.conjA) v.y = -v.y;
             }
             As[buf][kk][mm] = v;
-            int kb = e / BN, nn = e % BN;         // B: n fastest
+        }
+        for (int e = tid; e < BK * BN; e += THREADS) {
+            int kb = e / BN, nn = e % BN;          // B: n fastest
             int n = n0 + nn, k2 = k0 + kb;
             cplx w = make_double2(0.0, 0.0);
             if (n < g.N && k2 < K) {
@@ -75,17 +81,19 @@ __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
     __syncthreads();
     for (int k0 = 0; k0 < K; k0 += BK) {
         if (k0 + BK < K) load(k0 + BK, buf ^ 1);
+        if (active) {
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            cplx a[TM], bb[TN];
+            for (int kk = 0; kk < BK; ++kk) {
+                cplx a[TM], bb[TN];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + i * (BM / TM)];
+                for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + i * 16];
 #pragma unroll
-            for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx + j * (BN / TN)];
+                for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx + j * 16];
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) acc[i][j] = cmul_acc(acc[i][j], a[i], bb[j]);
+                    for (int j = 0; j < TN; ++j) acc[i][j] = cmul_acc(acc[i][j], a[i], bb[j]);
+            }
         }
         __syncthreads();
         buf ^= 1;
@@ -94,11 +102,11 @@ __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
     const bool beta0 = (g.beta.x == 0.0 && g.beta.y == 0.0);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        int m = m0 + ty + i * (BM / TM);
+        int m = m0 + ty + i * 16;
         if (m >= g.M) continue;
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-            int n = n0 + tx + j * (BN / TN);
+            int n = n0 + tx + j * 16;
             if (n >= g.N) continue;
             cplx* cp = C + m * g.c_m + n * g.c_n;
             cplx v = acc[i][j];
@@ -115,12 +123,21 @@ __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
     }
 }
 
+template <int BM, int BN>
+void launch_tile(const GemmArgs& g, cudaStream_t stream) {
+    long long batches = (long long)g.Bi * g.Bo;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)batches);
+    zgemm_f64_kernel<BM, BN><<<grid, THREADS, 0, stream>>>(g);
+}
+
 }  // namespace
 
 int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream) {
     if (g.M <= 0 || g.N <= 0 || g.Bi <= 0 || g.Bo <= 0) return 0;
-    long long batches = (long long)g.Bi * g.Bo;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)batches);
-    zgemm_f64_kernel<<<grid, THREADS, 0, stream>>>(g);
+    const bool sm = g.M <= 16, sn = g.N <= 16;
+    if (sm && sn) launch_tile<16, 16>(g, stream);
+    else if (sm) launch_tile<16, 64>(g, stream);
+    else if (sn) launch_tile<64, 16>(g, stream);
+    else launch_tile<64, 64>(g, stream);
     return 1;
 }

@@ -15,12 +15,14 @@
 //  1. pack_kernel: gathers the strided FP64 operand (any GemmArgs strides,
 //     optional conjugation, batches) into zero-padded K-major FP32 hi/lo
 //     planes; HBM bound, coalesced float2 stores.
-//  2. tcgen05 GEMM: one 128 x 64 tile of C~ per CTA, 6 warps.  Warp 4 issues
-//     TMA loads (128-byte swizzle, no multicast) into a 4-stage ring, warp 5
-//     issues 12 tcgen05.mma per 32-wide K slice into one of two TMEM
-//     accumulators and releases stages with tcgen05.commit; warps 0-3 drain
-//     finished K chunks from TMEM (tcgen05.ld 32x32b) into float-float sums
-//     and finally write alpha * C~ + beta * C in FP64.
+//  2. tcgen05 GEMM: persistent, one CTA per SM walking 128 x 64 tiles of C~,
+//     10 warps; the stage ring and TMEM buffers run on across tiles.  Warp 8 issues
+//     TMA loads (128-byte swizzle, no multicast) into a 4-stage ring, warp 9
+//     issues 12 tcgen05.mma per 32-wide K slice into one of four TMEM
+//     accumulators and releases stages with tcgen05.commit; warps 0-7 drain
+//     finished K chunks from TMEM (tcgen05.ld 32x32b, two warps per lane
+//     quadrant, 32 columns each) into float-float sums and finally write
+//     alpha * C~ + beta * C in FP64.
 //  Every mbarrier wait is bounded; on timeout the kernel sets an error flag,
 //  skips the rest, frees its TMEM and returns.
 #include "common.cuh"
@@ -122,13 +124,61 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Round a float to TF32 (10 explicit mantissa bits), to nearest, ties to even.
-__device__ __forceinline__ float tf32_rn(float f) {
-    uint32_t b = __float_as_uint(f);
-    if ((b & 0x7F800000u) == 0x7F800000u) return f;   // inf / nan unchanged
-    b += 0xFFFu + ((b >> 13) & 1u);
-    b &= 0xFFFFE000u;
-    return __uint_as_float(b);
+// Split an FP64 value into TF32-representable hi and lo with integer
+// operations only (GB300's FP64 pipe is the bottleneck of any FP64
+// arithmetic): hi = x rounded to 10 mantissa bits (to nearest, ties to even),
+// lo = the exact remainder x - hi rounded to 11 significant bits; |hi + lo - x|
+// <= 2^-23 |x|.  |x| < 2^-126 (and FP64 subnormals) give 0; inf/nan pass
+// through the conversion instruction.
+__device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(u >> 63);
+    const int e = (int)((u >> 52) & 0x7FF);
+    const unsigned long long mant = u & 0xFFFFFFFFFFFFFULL;
+    hi = 0.f;
+    lo = 0.f;
+    if (e == 0x7FF) {
+        hi = (float)x;
+        return;
+    }
+    if (e == 0) return;
+    unsigned long long m10 = mant >> 42;
+    const unsigned long long rem = mant & ((1ULL << 42) - 1);
+    const unsigned long long half = 1ULL << 41;
+    const bool up = rem > half || (rem == half && (m10 & 1ULL));
+    int fe = e - 1023 + 127;
+    if (up) {
+        m10 += 1;
+        if (m10 == (1ULL << 10)) {
+            m10 = 0;
+            fe += 1;
+        }
+    }
+    if (fe <= 0) return;
+    hi = __uint_as_float((sign << 31) | ((unsigned)fe << 23) | ((unsigned)m10 << 13));
+    const long long r = up ? (long long)rem - (long long)(1ULL << 42) : (long long)rem;
+    if (r == 0) return;
+    const unsigned lsign = sign ^ (r < 0 ? 1u : 0u);
+    const unsigned long long ar = (unsigned long long)(r < 0 ? -r : r);   // < 2^42
+    const int msb = 63 - __clzll((long long)ar);
+    int le = msb + (e - 1075) + 127;
+    unsigned long long m;
+    if (msb > 10) {
+        const int sh = msb - 10;
+        m = ar >> sh;
+        const unsigned long long rr = ar & ((1ULL << sh) - 1), h = 1ULL << (sh - 1);
+        if (rr > h || (rr == h && (m & 1ULL))) {
+            m += 1;
+            if (m == (1ULL << 11)) {
+                m >>= 1;
+                le += 1;
+            }
+        }
+    } else {
+        m = ar << (10 - msb);
+    }
+    if (le <= 0) return;
+    lo = __uint_as_float((lsign << 31) | ((unsigned)le << 23) | ((unsigned)(m & 0x3FFULL) << 13));
 }
 
 // ----------------------------------------------------------------- packing
@@ -161,10 +211,11 @@ __global__ void pack_kernel(PackArgs p) {
             int ki = k % p.Ki, ko = k / p.Ki;
             cplx v = p.src[bi * p.s_bi + bo * p.s_bo + r * p.s_r + ki * p.s_ki + ko * p.s_ko];
             re = v.x;
-            im = p.conj ? -v.y : v.y;
+            im = p.conj ? __longlong_as_double(__double_as_longlong(v.y) ^ (long long)0x8000000000000000ULL) : v.y;
         }
-        float rh = tf32_rn((float)re), ih = tf32_rn((float)im);
-        float rl = tf32_rn((float)(re - (double)rh)), il = tf32_rn((float)(im - (double)ih));
+        float rh, rl, ih, il;
+        split_tf32(re, rh, rl);
+        split_tf32(im, ih, il);
         long long plane_b = (long long)p.Rp * p.Kp * b;
         if (p.embed) {
             long long o0 = plane_b + (long long)(2 * r) * p.Kp + 2 * k;
@@ -191,19 +242,39 @@ __global__ void pack_kernel(PackArgs p) {
 // (Knuth TwoSum, ~2^-48 relative).  The error is then that of one short
 // chunk (~3e-7 relative), independent of K.
 constexpr int CHUNK_KB = 2;
-constexpr int DRAIN_THREADS = 128;                 // warps 0-3: TMEM lanes 0-127
-constexpr int GEMM_THREADS = DRAIN_THREADS + 64;   // warp 4: TMA, warp 5: MMA
+constexpr int NBUF = 4;                            // TMEM accumulators (NBUF * BN columns)
+constexpr int DRAIN_WARPS = 8;                     // warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..
+constexpr int DRAIN_THREADS = 32 * DRAIN_WARPS;
+constexpr int DCOLS = BN / (DRAIN_WARPS / 4);      // columns per drain thread
+constexpr int TMA_WARP = DRAIN_WARPS, MMA_WARP = DRAIN_WARPS + 1;
+constexpr int GEMM_THREADS = DRAIN_THREADS + 64;
 
 struct EpiArgs {
     cplx* C;
     long long c_m, c_n, c_bi, c_bo;
     int M, N, Bi;
     int swapped;          // P side holds the columns n of C (C^T computed)
-    int Pp, Qp;           // padded real rows per batch of P and Q
+    int Pp, Qp;           // packed-row stride per batch of P and Q (0 if shared)
     int nkb;              // K' / BK
+    int n_ptiles, n_qtiles, batches;   // tile grid; tile t: P tile fastest, then Q tile, then batch
     cplx alpha, beta;
+    int mode;             // 0: alpha = 1, beta = 0; 1: alpha = 1, beta = 1; 2: general
     int* err;
 };
+
+// double(f) built from f's bits with integer operations (GB300's FP64 pipe is
+// ~64x slower than its integer pipe; conversions would go through it).
+// Normal numbers and zero exactly; FP32 subnormals (< 1.2e-38) become zero;
+// inf/nan go through the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    uint32_t u = __float_as_uint(f);
+    uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0xFFu) return (double)f;
+    uint64_t sign = (uint64_t)(u >> 31) << 63;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    uint64_t bits = sign | ((uint64_t)(e + (1023u - 127u)) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     float s = __fadd_rn(hi, x);
@@ -220,22 +291,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* tfull = empty + STAGES;      // [2] chunk accumulated in TMEM buffer b
-    uint64_t* tempty = tfull + 2;          // [2] buffer b drained
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* tfull = empty + STAGES;      // [NBUF] chunk accumulated in TMEM buffer b
+    uint64_t* tempty = tfull + NBUF;       // [NBUF] buffer b drained
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + NBUF);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.z;
-    const int prow0 = b * ea.Pp + blockIdx.x * BM;   // P rows of this tile (packed buffer rows)
-    const int qrow0 = b * ea.Qp + blockIdx.y * BN;
     const int nchunk = (ea.nkb + CHUNK_KB - 1) / CHUNK_KB;
+    const long long ntiles = (long long)ea.batches * ea.n_qtiles * ea.n_ptiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], DRAIN_THREADS);
         }
@@ -243,7 +312,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2 * BN));
+                     "r"(NBUF * BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -251,98 +320,135 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
-        if (lane == 0) {   // TMA producer
-            for (int kb = 0; kb < ea.nkb; ++kb) {
-                int s = kb % STAGES, round = kb / STAGES;
-                if (kb >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1, ea.err)) break;
-                uint8_t* st = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(st, &mPh, &full[s], kb * BK, prow0);
-                tma_load_2d(st + A_TILE, &mPl, &full[s], kb * BK, prow0);
-                tma_load_2d(st + 2 * A_TILE, &mQh, &full[s], kb * BK, qrow0);
-                tma_load_2d(st + 2 * A_TILE + B_TILE, &mQl, &full[s], kb * BK, qrow0);
+    // persistent loop over tiles: t = blockIdx.x, blockIdx.x + gridDim.x, ...
+    if (warp == TMA_WARP) {
+        if (lane == 0) {   // TMA producer: one continuous stage ring across tiles
+            unsigned it = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int pt = (int)(t % ea.n_ptiles);
+                const long long rest = t / ea.n_ptiles;
+                const int qt = (int)(rest % ea.n_qtiles), b = (int)(rest / ea.n_qtiles);
+                const int prow0 = b * ea.Pp + pt * BM, qrow0 = b * ea.Qp + qt * BN;
+                for (int kb = 0; kb < ea.nkb; ++kb, ++it) {
+                    const unsigned s = it % STAGES, round = it / STAGES;
+                    if (it >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1, ea.err)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(st, &mPh, &full[s], kb * BK, prow0);
+                    tma_load_2d(st + A_TILE, &mPl, &full[s], kb * BK, prow0);
+                    tma_load_2d(st + 2 * A_TILE, &mQh, &full[s], kb * BK, qrow0);
+                    tma_load_2d(st + 2 * A_TILE + B_TILE, &mQl, &full[s], kb * BK, qrow0);
+                }
             }
         }
         __syncwarp();
-    } else if (warp == 5) {
+    } else if (warp == MMA_WARP) {
         if (lane == 0) {   // MMA issuer
+            unsigned it = 0, cg = 0;
             bool ok = true;
-            for (int c = 0; c < nchunk && ok; ++c) {
-                const int buf = c & 1;
-                const uint32_t dt = tmem + (uint32_t)(buf * BN);
-                if (c >= 2 && !mbar_wait(&tempty[buf], ((c >> 1) - 1) & 1, ea.err)) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int kb_end = min(ea.nkb, (c + 1) * CHUNK_KB);
-                for (int kb = c * CHUNK_KB; kb < kb_end; ++kb) {
-                    int s = kb % STAGES, round = kb / STAGES;
-                    if (!mbar_wait(&full[s], round & 1, ea.err)) {
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nchunk && ok; ++c, ++cg) {
+                    const unsigned buf = cg % NBUF;
+                    const uint32_t dt = tmem + (uint32_t)(buf * BN);
+                    if (cg >= NBUF && !mbar_wait(&tempty[buf], ((cg / NBUF) - 1) & 1, ea.err)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-                    uint64_t ph = sdesc(base), pl = sdesc(base + A_TILE);
-                    uint64_t qh = sdesc(base + 2 * A_TILE), ql = sdesc(base + 2 * A_TILE + B_TILE);
+                    const int kb_end = min(ea.nkb, (c + 1) * CHUNK_KB);
+                    for (int kb = c * CHUNK_KB; kb < kb_end; ++kb, ++it) {
+                        const unsigned s = it % STAGES, round = it / STAGES;
+                        if (!mbar_wait(&full[s], round & 1, ea.err)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+                        uint64_t ph = sdesc(base), pl = sdesc(base + A_TILE);
+                        uint64_t qh = sdesc(base + 2 * A_TILE), ql = sdesc(base + 2 * A_TILE + B_TILE);
 #pragma unroll
-                    for (int ks = 0; ks < BK / 8; ++ks) {
-                        uint64_t off = (uint64_t)(ks * 32) >> 4;   // 8 tf32 = 32 bytes along K
-                        uint32_t acc = (kb > c * CHUNK_KB || ks > 0) ? 1u : 0u;
-                        mma_tf32(dt, pl + off, qh + off, acc);
-                        mma_tf32(dt, ph + off, ql + off, 1u);
-                        mma_tf32(dt, ph + off, qh + off, 1u);
+                        for (int ks = 0; ks < BK / 8; ++ks) {
+                            uint64_t off = (uint64_t)(ks * 32) >> 4;   // 8 tf32 = 32 bytes along K
+                            uint32_t acc = (kb > c * CHUNK_KB || ks > 0) ? 1u : 0u;
+                            mma_tf32(dt, pl + off, qh + off, acc);
+                            mma_tf32(dt, ph + off, ql + off, 1u);
+                            mma_tf32(dt, ph + off, qh + off, 1u);
+                        }
+                        mma_commit(&empty[s]);
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit(&tfull[buf]);
                 }
-                mma_commit(&tfull[buf]);
             }
         }
         __syncwarp();
     } else {
-        // drain warps 0-3: thread = TMEM lane = tile row
-        float hi[BN], lo[BN];
-#pragma unroll
-        for (int j = 0; j < BN; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+        // drain warps: thread = TMEM lane (tile row), DCOLS columns per thread
+        const int quad = warp & 3, col0 = (warp >> 2) * DCOLS;
+        const bool beta0 = (ea.beta.x == 0.0 && ea.beta.y == 0.0);
+        unsigned cg = 0;
         bool ok = true;
-        for (int c = 0; c < nchunk; ++c) {
-            const int buf = c & 1;
-            if (!mbar_wait(&tfull[buf], (c >> 1) & 1, ea.err)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int pt = (int)(t % ea.n_ptiles);
+            const long long rest = t / ea.n_ptiles;
+            const int qt = (int)(rest % ea.n_qtiles), b = (int)(rest / ea.n_qtiles);
+            float hi[DCOLS], lo[DCOLS];
 #pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * BN + c0), v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) two_sum_acc(hi[c0 + j], lo[c0 + j], v[j]);
+            for (int j = 0; j < DCOLS; ++j) {
+                hi[j] = 0.f;
+                lo[j] = 0.f;
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
-        }
-        if (ok) {
-            const int trow = warp * 32 + lane;                  // row of C~ inside the tile
-            const int prow = blockIdx.x * BM + trow;            // P real row within the batch
+            for (int c = 0; c < nchunk; ++c, ++cg) {
+                const unsigned buf = cg % NBUF;
+                if (!mbar_wait(&tfull[buf], (cg / NBUF) & 1, ea.err)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int c0 = 0; c0 < DCOLS; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + col0 + c0), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) two_sum_acc(hi[c0 + j], lo[c0 + j], v[j]);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
+            }
+            if (!ok) break;
+            const int trow = quad * 32 + lane;                  // row of C~ inside the tile
+            const int prow = pt * BM + trow;                    // P real row within the batch
             const int pr = prow >> 1;                           // complex row of P
             const int bi = b % ea.Bi, bo = b / ea.Bi;
             cplx* C = ea.C + bi * ea.c_bi + bo * ea.c_bo;
-            const bool beta0 = (ea.beta.x == 0.0 && ea.beta.y == 0.0);
 #pragma unroll
-            for (int j = 0; j < BN; ++j) {
-                double val = (double)hi[j] + (double)lo[j];
+            for (int j = 0; j < DCOLS; ++j) {
+                double val = f32_to_f64(hi[j]) + f32_to_f64(lo[j]);
                 double other = __shfl_xor_sync(0xffffffffu, val, 1);
                 if (lane & 1) continue;
-                int qn = blockIdx.y * BN + j;                   // Q row = the other index
+                int qn = qt * BN + col0 + j;                    // Q row = the other index
                 int m = ea.swapped ? qn : pr;
                 int n = ea.swapped ? pr : qn;
                 if (m >= ea.M || n >= ea.N) continue;
                 double re = val, im = other;
                 cplx* cp = C + m * ea.c_m + n * ea.c_n;
                 cplx r;
-                r.x = ea.alpha.x * re - ea.alpha.y * im;
-                r.y = ea.alpha.x * im + ea.alpha.y * re;
-                if (!beta0) {
+                if (ea.mode == 0) {                 // alpha = 1, beta = 0
+                    r = make_double2(re, im);
+                } else if (ea.mode == 1) {          // alpha = 1, beta = 1
                     cplx o = *cp;
-                    r.x += ea.beta.x * o.x - ea.beta.y * o.y;
-                    r.y += ea.beta.x * o.y + ea.beta.y * o.x;
+                    r = make_double2(o.x + re, o.y + im);
+                } else {
+                    r.x = ea.alpha.x * re - ea.alpha.y * im;
+                    r.y = ea.alpha.x * im + ea.alpha.y * re;
+                    if (!beta0) {
+                        cplx o = *cp;
+                        r.x += ea.beta.x * o.x - ea.beta.y * o.y;
+                        r.y += ea.beta.x * o.y + ea.beta.y * o.x;
+                    }
                 }
                 *cp = r;
             }
@@ -352,7 +458,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NBUF * BN));
     }
 }
 
@@ -389,6 +495,7 @@ inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m
 struct Plan {
     bool ok = false;
     bool swapped = false;
+    bool p_bcast = false, q_bcast = false;   // operand identical in every batch: packed once
     int Rp_rows = 0, Rq_rows = 0;    // complex rows of P and Q
     int Pp = 0, Qp = 0, Kp = 0;      // padded real rows / K'
     long long batches = 0;
@@ -408,7 +515,12 @@ Plan plan_for(const GemmArgs& g) {
     pl.Kp = (int)round_up(2 * K, BK);
     pl.batches = (long long)g.Bi * g.Bo;
     if (pl.batches > 65535 || pl.Qp / BN > 65535) return pl;
-    size_t pe = (size_t)pl.batches * pl.Pp * pl.Kp, qe = (size_t)pl.batches * pl.Qp * pl.Kp;
+    const bool a_b = (g.a_bi == 0 || g.Bi == 1) && (g.a_bo == 0 || g.Bo == 1);
+    const bool b_b = (g.b_bi == 0 || g.Bi == 1) && (g.b_bo == 0 || g.Bo == 1);
+    pl.p_bcast = pl.swapped ? b_b : a_b;
+    pl.q_bcast = pl.swapped ? a_b : b_b;
+    size_t pe = (size_t)(pl.p_bcast ? 1 : pl.batches) * pl.Pp * pl.Kp;
+    size_t qe = (size_t)(pl.q_bcast ? 1 : pl.batches) * pl.Qp * pl.Kp;
     pl.bytes = 2 * (pe + qe) * sizeof(float) + 256;
     pl.ok = true;
     return pl;
@@ -428,7 +540,8 @@ int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, s
     Plan pl = plan_for(g);
     if (!pl.ok || !encode_fn()) return -1;
     if (!workspace || workspace_bytes < pl.bytes) return -2;
-    size_t pe = (size_t)pl.batches * pl.Pp * pl.Kp, qe = (size_t)pl.batches * pl.Qp * pl.Kp;
+    const long long np_b = pl.p_bcast ? 1 : pl.batches, nq_b = pl.q_bcast ? 1 : pl.batches;
+    size_t pe = (size_t)np_b * pl.Pp * pl.Kp, qe = (size_t)nq_b * pl.Qp * pl.Kp;
     float* Ph = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(workspace) + 256);
     float* Pl = Ph + pe;
     float* Qh = Pl + pe;
@@ -448,9 +561,11 @@ int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, s
     PackArgs& Q = pl.swapped ? pa : pb;
     P.embed = 1; P.Rp = pl.Pp; P.hi = Ph; P.lo = Pl;
     Q.embed = 0; Q.Rp = pl.Qp; Q.hi = Qh; Q.lo = Ql;
+    if (pl.p_bcast) { P.Bi = 1; P.Bo = 1; }
+    if (pl.q_bcast) { Q.Bi = 1; Q.Bo = 1; }
     int launches = 0;
     for (PackArgs* p : {&P, &Q}) {
-        long long total = (long long)(p->embed ? p->Rp / 2 : p->Rp) * (p->Kp / 2) * pl.batches;
+        long long total = (long long)(p->embed ? p->Rp / 2 : p->Rp) * (p->Kp / 2) * p->Bi * p->Bo;
         long long grid = std::min<long long>((total + 255) / 256, 152LL * 16);
         pack_kernel<<<(unsigned)grid, 256, 0, stream>>>(*p);
         ++launches;
@@ -467,26 +582,42 @@ int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, si
         cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         attr_set = true;
     }
-    size_t pe = (size_t)pl.batches * pl.Pp * pl.Kp, qe = (size_t)pl.batches * pl.Qp * pl.Kp;
+    const long long pb = pl.p_bcast ? 1 : pl.batches, qb = pl.q_bcast ? 1 : pl.batches;
+    size_t pe = (size_t)pb * pl.Pp * pl.Kp, qe = (size_t)qb * pl.Qp * pl.Kp;
     int* err = reinterpret_cast<int*>(workspace);          // first 256 bytes: error flag
     float* Ph = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(workspace) + 256);
     float* Pl = Ph + pe;
     float* Qh = Pl + pe;
     float* Ql = Qh + qe;
     CUtensorMap mPh, mPl, mQh, mQl;
-    if (!make_map(&mPh, Ph, pl.batches * pl.Pp, pl.Kp, BM) || !make_map(&mPl, Pl, pl.batches * pl.Pp, pl.Kp, BM) ||
-        !make_map(&mQh, Qh, pl.batches * pl.Qp, pl.Kp, BN) || !make_map(&mQl, Ql, pl.batches * pl.Qp, pl.Kp, BN))
+    if (!make_map(&mPh, Ph, pb * pl.Pp, pl.Kp, BM) || !make_map(&mPl, Pl, pb * pl.Pp, pl.Kp, BM) ||
+        !make_map(&mQh, Qh, qb * pl.Qp, pl.Kp, BN) || !make_map(&mQl, Ql, qb * pl.Qp, pl.Kp, BN))
         return -1;
     EpiArgs ea;
     ea.C = g.C; ea.c_m = g.c_m; ea.c_n = g.c_n; ea.c_bi = g.c_bi; ea.c_bo = g.c_bo;
     ea.M = g.M; ea.N = g.N; ea.Bi = g.Bi;
     ea.swapped = pl.swapped;
-    ea.Pp = pl.Pp; ea.Qp = pl.Qp;
+    ea.Pp = pl.p_bcast ? 0 : pl.Pp;   // batch stride of the packed rows (0: shared)
+    ea.Qp = pl.q_bcast ? 0 : pl.Qp;
     ea.nkb = pl.Kp / BK;
     ea.alpha = g.alpha; ea.beta = g.beta;
+    const bool a1 = g.alpha.x == 1.0 && g.alpha.y == 0.0;
+    ea.mode = (a1 && g.beta.x == 0.0 && g.beta.y == 0.0) ? 0 : (a1 && g.beta.x == 1.0 && g.beta.y == 0.0) ? 1 : 2;
     ea.err = err;
-    // P tiles fastest: CTAs sharing a Q tile run together and hit it in L2
-    dim3 grid(pl.Pp / BM, pl.Qp / BN, (unsigned)pl.batches);
+    // persistent: one CTA per SM walks the tiles, P tiles fastest so CTAs
+    // sharing a Q tile run together and hit it in L2
+    ea.n_ptiles = pl.Pp / BM;
+    ea.n_qtiles = pl.Qp / BN;
+    ea.batches = (int)pl.batches;
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    long long ntiles = (long long)ea.n_ptiles * ea.n_qtiles * pl.batches;
+    unsigned grid = (unsigned)std::min<long long>(ntiles, n_sm);
     tc_gemm_kernel<<<grid, GEMM_THREADS, SMEM_BYTES, stream>>>(mPh, mPl, mQh, mQl, ea);
     return 1;
 }

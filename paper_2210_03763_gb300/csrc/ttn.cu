@@ -14,6 +14,7 @@
 #include "../../include/ttn.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -147,7 +148,8 @@ struct ttn_ctx {
 
     // kernel-level profile: event pairs around launches while enabled
     bool profiling = false;
-    struct ProfRec { int kind; cudaEvent_t e0, e1; double flops, bytes; };
+    struct ProfRec { int kind; cudaEvent_t e0, e1; double flops, bytes; int shape[4]; };
+    std::vector<std::array<double, 7>> prof_last;   // kind, M, N, K, batch, ms, flops of the last profile
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_next = 0;
@@ -213,8 +215,16 @@ struct ProfScope {
     ttn_ctx* c;
     int kind;
     double flops, bytes;
+    int shape[4] = {0, 0, 0, 0};
     cudaEvent_t e0 = nullptr;
-    ProfScope(ttn_ctx* c_, int k, double f = 0, double b = 0) : c(c_), kind(k), flops(f), bytes(b) {
+    ProfScope(ttn_ctx* c_, int k, double f = 0, double b = 0, const GemmArgs* g = nullptr)
+        : c(c_), kind(k), flops(f), bytes(b) {
+        if (g) {
+            shape[0] = g->M;
+            shape[1] = g->N;
+            shape[2] = g->Ki * g->Ko;
+            shape[3] = g->Bi * g->Bo;
+        }
         if (c->profiling) {
             e0 = next_event(c);
             CUDA_OK(cudaEventRecord(e0, c->stream));
@@ -224,7 +234,7 @@ struct ProfScope {
         if (c->profiling && e0) {
             cudaEvent_t e1 = next_event(c);
             cudaEventRecord(e1, c->stream);
-            c->prof.push_back({kind, e0, e1, flops, bytes});
+            c->prof.push_back({kind, e0, e1, flops, bytes, {shape[0], shape[1], shape[2], shape[3]}});
         }
     }
 };
@@ -256,11 +266,11 @@ void gemm(ttn_ctx* c, const GemmArgs& g) {
             double nb = (double)g.Bi * g.Bo;
             double pack_bytes = nb * ((double)g.M + g.N) * g.Ki * (double)g.Ko * 16.0 + 0.5 * need;
             {
-                ProfScope ps(c, PK_PACK, 0.0, pack_bytes);
+                ProfScope ps(c, PK_PACK, 0.0, pack_bytes, &g);
                 n = launch_split_pack(g, c->stream, c->split_ws, c->split_cap);
             }
             if (n >= 0) {
-                ProfScope ps(c, PK_TC, fl, 0.5 * need + nb * (double)g.M * g.N * 16.0);
+                ProfScope ps(c, PK_TC, fl, 0.5 * need + nb * (double)g.M * g.N * 16.0, &g);
                 int m = launch_split_mma(g, c->stream, c->split_ws, c->split_cap);
                 if (m < 0) throw TtnError(TTN_ERR_CUDA, "split GEMM launch failed after packing");
                 n += m;
@@ -268,7 +278,7 @@ void gemm(ttn_ctx* c, const GemmArgs& g) {
         }
     }
     if (n < 0) {
-        ProfScope ps(c, PK_F64, fl, 0.0);
+        ProfScope ps(c, PK_F64, fl, 0.0, &g);
         n = launch_zgemm_f64(g, c->stream);
     }
     c->stats[3] += n;
@@ -413,6 +423,7 @@ void build_G(ttn_ctx* c, const Env& a, const Env& b, cplx* G) {
     g.A = b.nops; g.a_m = 1; g.a_ki = DD;
     g.B = vsub_for(c, a, b); g.b_ki = 1; g.b_n = nbs;
     g.C = G; g.c_m = 1; g.c_n = DD;
+    ProfScope ps(c, PK_F64, gemm_flops(g), 0.0, &g);
     c->stats[3] += launch_zgemm_f64(g, c->stream);   // tiny, keep FP64
 }
 
@@ -919,13 +930,24 @@ void allocate(ttn_ctx* c) {
     c->kh2 = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1));
     c->kpart = (cplx*)dalloc(c, sizeof(cplx) * 2 * RED_BLOCKS * (MAX_CHI + 2));
     c->kpn = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
-    c->qr.part = (cplx*)dalloc(c, sizeof(cplx) * 2 * RED_BLOCKS * (MAX_CHI + 2));
+    long long gq = 1;   // QR row blocks: max over nodes and legs of ceil((s / d_leg) / QR_ROWS)
+    for (int k = 0; k < nn; ++k)
+        for (int u = 0; u < 3; ++u)
+            gq = std::max(gq, (c->nodes[k].s / c->nodes[k].d[u] + QR_ROWS - 1) / QR_ROWS);
+    c->qr.part = (cplx*)dalloc(c, sizeof(cplx) * 2 * gq * (MAX_CHI + 2));
     c->qr.h = (cplx*)dalloc(c, sizeof(cplx) * (MAX_CHI + 2));
-    c->qr.pnorm = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
+    c->qr.pnorm = (double*)dalloc(c, sizeof(double) * std::max<long long>(gq, QR_FROB_BLOCKS));
     c->qr.scal = (double*)dalloc(c, sizeof(double) * 8);
     c->qr.flags = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
     c->qr.rownorm = (double*)dalloc(c, sizeof(double) * c->smax);
     c->qr.pick = (int*)dalloc(c, sizeof(int) * 4);
+    c->qr.kept = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
+    c->qr.dep = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
+    c->qr.acc_rows = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
+    c->qr.Y = (cplx*)dalloc(c, sizeof(cplx) * QR_SC_MAXR * (MAX_CHI + 2));
+    c->qr.nu = (double*)dalloc(c, sizeof(double) * (MAX_CHI + 2));
+    c->qr.row_rank = (int*)dalloc(c, sizeof(int) * c->smax);
+    c->qr.cand_used = (int*)dalloc(c, sizeof(int) * c->smax);
     c->d_coef = (double*)dalloc(c, sizeof(double) * 5 * c->N);
     c->h_coef.assign(5 * c->N, 0.0);
     CUDA_OK(cudaMallocHost(&c->hflag, 4 * sizeof(int)));
@@ -1629,9 +1651,12 @@ ttn_status ttn_profile_end(ttn_ctx* c, double* out, int n) {
         c->profiling = false;
         CUDA_OK(cudaStreamSynchronize(c->stream));
         for (int i = 0; i < 4 * PK_N; ++i) out[i] = 0.0;
+        c->prof_last.clear();
         for (auto& r : c->prof) {
             float ms = 0.f;
             CUDA_OK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+            c->prof_last.push_back({(double)r.kind, (double)r.shape[0], (double)r.shape[1], (double)r.shape[2],
+                                    (double)r.shape[3], (double)ms, r.flops});
             out[4 * r.kind + 0] += 1.0;
             out[4 * r.kind + 1] += ms;
             out[4 * r.kind + 2] += r.flops;
@@ -1699,6 +1724,15 @@ ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned lo
         if (tmp.split_ws) cudaFree(tmp.split_ws);
         tmp.split_ws = nullptr;
     });
+}
+
+ttn_status ttn_profile_records(const ttn_ctx* c, double* out, int max_records, int* n_records) {
+    if (!c || !n_records) return TTN_ERR_ARG;
+    *n_records = (int)c->prof_last.size();
+    if (out)
+        for (int i = 0; i < std::min(max_records, *n_records); ++i)
+            for (int j = 0; j < 7; ++j) out[7 * i + j] = c->prof_last[i][j];
+    return TTN_OK;
 }
 
 ttn_status ttn_get_stats(const ttn_ctx* c, int64_t* out) {

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("ttn_selftest_contract", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_ulonglong, ctypes.c_int, _D]),
     ("ttn_profile_end", ctypes.c_int, [_P, _D, ctypes.c_int]),
+    ("ttn_profile_records", ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
     ("ttn_reset_stats", ctypes.c_int, [_P]),
     ("ttn_contract_split_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
 ]
@@ -274,6 +275,14 @@ class TTN:
         self._check(self.lib.ttn_profile_end(self.h, _dptr(out), 16), "profile_end")
         return {k: {"launches": int(out[4 * i]), "ms": out[4 * i + 1], "flops": out[4 * i + 2],
                     "bytes": out[4 * i + 3]} for i, k in enumerate(self.PROFILE_KINDS)}
+
+    def profile_records(self):
+        """(kind, M, N, K, batches, ms, flops) per launch of the last profile."""
+        n = ctypes.c_int()
+        self._check(self.lib.ttn_profile_records(self.h, None, 0, ctypes.byref(n)), "profile_records")
+        out = np.zeros(7 * max(1, n.value))
+        self._check(self.lib.ttn_profile_records(self.h, _dptr(out), n.value, ctypes.byref(n)), "profile_records")
+        return out[:7 * n.value].reshape(n.value, 7)
 
     def reset_stats(self):
         self._check(self.lib.ttn_reset_stats(self.h), "reset_stats")
