@@ -125,7 +125,9 @@ def time_steps(torch, g, stream, k, profile=False):
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(k):
+        torch.cuda.nvtx.range_push("bench_step")   # lets a profiler capture exactly the timed steps
         g.step(DT)
+        torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     prof = g.profile_end() if profile else None
@@ -246,10 +248,12 @@ def main():
     from paper_2210_03763_gb300 import native
 
     stream = torch.cuda.current_stream()
+    free0, total = torch.cuda.mem_get_info()
     g = make_ctx(native, native.SPLIT_TF32X3, stream)
     for _ in range(args.warmup):
         g.step(DT)
     torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()   # after warm-up: workspaces have grown to size
     if dist:
         dist.barrier()
     clk = ClockSampler(local)
@@ -275,8 +279,10 @@ def main():
         pops = g.measure(2)
     torch.cuda.synchronize()
     e2e_secs = time.perf_counter() - t0
-    e2e = {"value": args.e2e_steps / e2e_secs, "unit": "steps/s",
-           "h2d_bytes_per_step": int(pulse_host.nbytes), "d2h_bytes_per_step": int(pops.nbytes)}
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = {"value": args.e2e_steps / e2e_secs, "unit": "steps/s",
+               "h2d_bytes_per_step": int(pulse_host.nbytes), "d2h_bytes_per_step": int(pops.nbytes)}
 
     pk, peak_kind = peaks()
     tc = prof["tc_gemm"]
@@ -298,7 +304,8 @@ def main():
               "data": "synthetic",
               "config": {"workload": WORKLOAD, "lattice": "8x8", "chi": CHI, "dt": DT,
                          "parallelism": "replicas" if world > 1 else "single",
-                         "l2": "working set (node tensors, environments, Krylov basis) > 129 MB L2"},
+                         "l2": "working set (node tensors, environments, Krylov basis) > 129 MB L2",
+                         "device_mem_gb": round((free0 - free1) / 1e9, 2)},
               "gpu_launches": int(stats["launches"]), "clocks": clocks, "e2e": e2e, "roofline": roof,
               "profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()},
               "dominant_kernel_class": dominant[0],

@@ -187,9 +187,23 @@ ttn_status ttn_profile_begin(ttn_ctx* ctx);
 ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned long long seed,
                                  int tf32_exact, double* rel_err);
 ttn_status ttn_profile_end(ttn_ctx* ctx, double* out, int n);
+/* Self-test and timing hook of the gauge-move QR (Sec. "Tensor network
+ * simulations": the orthogonality centre moves by a QR of the node tensor),
+ * no context needed.  A (host, M x D complex as interleaved (re, im) doubles,
+ * column-major, lda = M, M >= D, D <= 256, M * D <= 2^26) is copied to the
+ * device and factorised there as A = Q R by CGS2 with the deterministic
+ * completion of dependent columns (residual <= 1e-10 ||A||_F; candidates
+ * cand[0..ncand) in order, or rows 0..M-1 when cand is NULL); Q (M x D) and
+ * R (D x D, upper triangular, real non-negative diagonal) are written to host
+ * buffers of the caller; *n_dependent (may be NULL) receives the number of
+ * completed columns and *ms (may be NULL) the device time of the
+ * factorisation.  Bad sizes or candidate rows -> TTN_ERR_ARG. */
+ttn_status ttn_selftest_qr(const double* A, int M, int D, const int* cand, int ncand, double* Q, double* R,
+                           int* n_dependent, float* ms);
 /* Per-launch records of the last profile: 7 doubles each (kind, M, N, K,
  * batches, ms, algorithmic flops; K and batches are the products of the
- * two-level extents).  *n_records receives the count; at most max_records
+ * two-level extents; for a QR record: kind 3, rows, columns, dependent
+ * columns, 1).  *n_records receives the count; at most max_records
  * are written to out (which may be NULL to query the count). */
 ttn_status ttn_profile_records(const ttn_ctx* ctx, double* out, int max_records, int* n_records);
 ttn_status ttn_reset_stats(ttn_ctx* ctx);

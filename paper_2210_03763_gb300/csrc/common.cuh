@@ -83,8 +83,8 @@ int k_check_finite(const cplx* x, long long n, int* flag, cudaStream_t s);
 constexpr int QR_ROWS = 128;
 constexpr int QR_FROB_BLOCKS = 1024;
 struct QrScratch {
-    cplx* part;         // RED_BLOCKS * (D + 1) partial dots
-    cplx* h;            // D + 1 projections
+    cplx* part;         // 2 * row blocks * (2 * MAX_CHI + 4) partial sums
+    cplx* h;            // 2 * (D + 2) projection coefficients
     double* pnorm;      // RED_BLOCKS partial norms
     double* scal;       // scalars: [0] ||A||_F^2, [1] current column norm, ...
     int* flags;         // per-column dependent flags (D)
@@ -99,10 +99,14 @@ struct QrScratch {
     double* nu;         // D: residual norms
     int* row_rank;      // M: step at which a row was accepted (INT_MAX: never)
     int* cand_used;     // M: candidate accepted flags
+    unsigned* bar;      // 2: grid barrier of the cooperative column loop
+    int* err;           // set when a bounded device wait gave up
 };
 constexpr int QR_SC_MAXR = 64;   // structured completion when the kept rank r <= this
 // In-place QR of the column-major M x D matrix A (lda = M): A <- Q, R (D x D,
 // column-major) written.  cand[0..ncand) is the completion candidate order.
+// Returns the number of kernels launched, or -1 when a bounded device wait
+// of the cooperative column loop gave up (A and R are then undefined).
 int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand,
             QrScratch& ws, cudaStream_t s, int* n_dependent_host);
 

@@ -126,34 +126,38 @@ __device__ double decide(int kd, const double* pnorm, int G, double* scal, cplx*
     return dep ? 0.0 : 1.0 / nrm;
 }
 
-// K1 for column k >= 1
-__global__ void __launch_bounds__(QB) qr_k1(const cplx* A, long long M, int D, int k, const double* pnorm, int G,
-                                            double* scal, cplx* R, int* flags, cplx* part) {
-    __shared__ int szero[MAXD];
-    __shared__ cplx wsum[MAXD][QB / 32];
-    __shared__ double sfac;
-    if (threadIdx.x == 0) sfac = decide(k - 1, pnorm, G, scal, R, D, flags);
-    for (int i = threadIdx.x; i < k - 1; i += QB) szero[i] = flags[i];
+// Shared memory of one column phase.
+struct PhaseSmem {
+    int szero[MAXD];
+    cplx h[MAXD];
+    cplx wsum[MAXD][QB / 32];
+    double sh[QB / 32];
+    double sfac;
+};
+
+// K1 for column k >= 1: decide column k-1, dots of a_k with columns < k
+__device__ void phase_k1(const cplx* A, long long M, int D, int k, const double* pnorm, int G, double* scal, cplx* R,
+                         int* flags, cplx* part, PhaseSmem& sm) {
+    if (threadIdx.x == 0) sm.sfac = decide(k - 1, pnorm, G, scal, R, D, flags);
+    for (int i = threadIdx.x; i < k - 1; i += QB) sm.szero[i] = flags[i];
     __syncthreads();
-    if (threadIdx.x == 0) szero[k - 1] = (sfac == 0.0);
+    if (threadIdx.x == 0) sm.szero[k - 1] = (sm.sfac == 0.0);
     __syncthreads();
     long long r = blockIdx.x * (long long)QB + threadIdx.x;
     bool valid = r < M;
     cplx w = valid ? A[r + (long long)k * M] : make_double2(0.0, 0.0);
-    block_dots(A, M, k, szero, w, valid, r, k - 1, sfac, wsum, part, G, -1);
+    block_dots(A, M, k, sm.szero, w, valid, r, k - 1, sm.sfac, sm.wsum, part, G, -1);
+    __syncthreads();
 }
 
 // K2: scale column k-1, h = sum of partials, a_k -= sum_i A_i h_i, dots again
-__global__ void __launch_bounds__(QB) qr_k2(cplx* A, long long M, int D, int k, const int* flags, const double* scal,
-                                            const cplx* part_in, cplx* part_out, cplx* R, int G) {
-    __shared__ int szero[MAXD];
-    __shared__ cplx h[MAXD];
-    __shared__ cplx wsum[MAXD][QB / 32];
+__device__ void phase_k2(cplx* A, long long M, int D, int k, const int* flags, const double* scal,
+                         const cplx* part_in, cplx* part_out, cplx* R, int G, PhaseSmem& sm) {
     const double fac = scal[1];
     for (int i = threadIdx.x; i < k; i += QB) {
-        szero[i] = flags[i];
-        h[i] = szero[i] ? make_double2(0.0, 0.0) : sum_partials(part_in, i, G);
-        if (blockIdx.x == 0) R[(long long)k * D + i] = h[i];
+        sm.szero[i] = flags[i];
+        sm.h[i] = sm.szero[i] ? make_double2(0.0, 0.0) : sum_partials(part_in, i, G);
+        if (blockIdx.x == 0) R[(long long)k * D + i] = sm.h[i];
     }
     __syncthreads();
     long long r = blockIdx.x * (long long)QB + threadIdx.x;
@@ -167,26 +171,24 @@ __global__ void __launch_bounds__(QB) qr_k2(cplx* A, long long M, int D, int k, 
         *pk1 = v;   // column k-1 is final now (zero if dependent)
         w = A[r + (long long)k * M];
         for (int i = 0; i < k; ++i) {
-            if (szero[i]) continue;
-            cplx a = A[r + (long long)i * M], hi = h[i];
+            if (sm.szero[i]) continue;
+            cplx a = A[r + (long long)i * M], hi = sm.h[i];
             w.x -= a.x * hi.x - a.y * hi.y;
             w.y -= a.x * hi.y + a.y * hi.x;
         }
         A[r + (long long)k * M] = w;
     }
-    block_dots(A, M, k, szero, w, valid, r, -1, 1.0, wsum, part_out, G, -1);
+    block_dots(A, M, k, sm.szero, w, valid, r, -1, 1.0, sm.wsum, part_out, G, -1);
+    __syncthreads();
 }
 
 // K3: h2 = sum, R[:k, k] += h2, a_k -= Q h2, norm partials
-__global__ void __launch_bounds__(QB) qr_k3(cplx* A, long long M, int D, int k, const int* flags, const cplx* part_in,
-                                            cplx* R, double* pnorm, int G) {
-    __shared__ int szero[MAXD];
-    __shared__ cplx h[MAXD];
-    __shared__ double sh[QB / 32];
+__device__ void phase_k3(cplx* A, long long M, int D, int k, const int* flags, const cplx* part_in, cplx* R,
+                         double* pnorm, int G, PhaseSmem& sm) {
     for (int i = threadIdx.x; i < k; i += QB) {
-        szero[i] = flags[i];
-        h[i] = szero[i] ? make_double2(0.0, 0.0) : sum_partials(part_in, i, G);
-        if (blockIdx.x == 0) R[(long long)k * D + i] = cadd(R[(long long)k * D + i], h[i]);
+        sm.szero[i] = flags[i];
+        sm.h[i] = sm.szero[i] ? make_double2(0.0, 0.0) : sum_partials(part_in, i, G);
+        if (blockIdx.x == 0) R[(long long)k * D + i] = cadd(R[(long long)k * D + i], sm.h[i]);
     }
     __syncthreads();
     long long r = blockIdx.x * (long long)QB + threadIdx.x;
@@ -194,16 +196,402 @@ __global__ void __launch_bounds__(QB) qr_k3(cplx* A, long long M, int D, int k, 
     if (r < M) {
         cplx w = A[r + (long long)k * M];
         for (int i = 0; i < k; ++i) {
-            if (szero[i]) continue;
-            cplx a = A[r + (long long)i * M], hi = h[i];
+            if (sm.szero[i]) continue;
+            cplx a = A[r + (long long)i * M], hi = sm.h[i];
             w.x -= a.x * hi.x - a.y * hi.y;
             w.y -= a.x * hi.y + a.y * hi.x;
         }
         A[r + (long long)k * M] = w;
         s = w.x * w.x + w.y * w.y;
     }
-    s = block_sum_d(s, sh);
+    s = block_sum_d(s, sm.sh);
     if (threadIdx.x == 0) pnorm[blockIdx.x] = s;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(QB) qr_k1(const cplx* A, long long M, int D, int k, const double* pnorm, int G,
+                                            double* scal, cplx* R, int* flags, cplx* part) {
+    __shared__ PhaseSmem sm;
+    phase_k1(A, M, D, k, pnorm, G, scal, R, flags, part, sm);
+}
+
+__global__ void __launch_bounds__(QB) qr_k2(cplx* A, long long M, int D, int k, const int* flags, const double* scal,
+                                            const cplx* part_in, cplx* part_out, cplx* R, int G) {
+    __shared__ PhaseSmem sm;
+    phase_k2(A, M, D, k, flags, scal, part_in, part_out, R, G, sm);
+}
+
+__global__ void __launch_bounds__(QB) qr_k3(cplx* A, long long M, int D, int k, const int* flags, const cplx* part_in,
+                                            cplx* R, double* pnorm, int G) {
+    __shared__ PhaseSmem sm;
+    phase_k3(A, M, D, k, flags, part_in, R, pnorm, G, sm);
+}
+
+// ------------------------------------------------- cooperative column loop
+// The whole CGS2 column loop in one cooperative launch (all row blocks
+// co-resident).  Every block owns QB rows and only ever touches those rows of
+// A; blocks exchange per-block partial sums through global memory at grid
+// synchronisations, and every block sums them in the same fixed order, so all
+// blocks take identical decisions and runs are reproducible.
+//
+// One synchronisation per column.  At X(k) the blocks sum, for the kept
+// columns Q (those before k):
+//   h2 = Q^H v1_k,  g = Q^H a_{k+1},  c = v1_k^H a_{k+1},  |v1_k|^2
+// where v1_k = a_k - Q h1_k is column k after its first pass.  Then
+//   |v2_k|^2 = |v1_k|^2 - |h2|^2  decides column k (exact for orthonormal Q;
+//     where the decision is close, |h2| is at rounding level of |a_k| and the
+//     difference is far below the threshold),
+//   q_k = (v1_k - Q h2) / |v2_k|,
+//   h1_{k+1} = [g ; (c - h2^H g) / |v2_k|]  (the component of a_{k+1} along
+//     q_k follows from the sums already at hand, no second synchronisation),
+//   v1_{k+1} = a_{k+1} - [Q q_k] h1_{k+1}.
+// So both Gram-Schmidt passes of every column are done against the stored
+// columns, as in plain CGS2, with the second pass of column k and the first
+// of column k+1 sharing one reduction.  Only kept columns take part, so a
+// low-rank matrix costs O(M D rank) flops; the first QC_MAX kept columns of a
+// block's rows stay in shared memory.
+constexpr long long QR_BAR_SPINS = 1LL << 22;
+constexpr int QCS = QB + 1;            // cache column stride (odd: no bank conflicts)
+constexpr int QC_MAX = 32;             // kept columns cached in shared memory
+constexpr int PSTRIDE = 2 * MAXD + 4;  // partial row length
+
+struct CoopSm {
+    int nz[MAXD];             // kept columns so far, in order
+    cplx h1s[MAXD + 1];       // first-pass coefficients of the current column
+    cplx hb[PSTRIDE];         // summed partials of the current synchronisation
+    cplx v1[QB];              // this block's rows of v1_k
+    cplx an[QB];              // this block's rows of a_{k+1}
+    cplx red[2 * QB];
+    double d0[QB / 32], d1[QB / 32], d2[QB / 32];
+    double fro2, scale;
+    cplx hk;
+    int nnz, ok, dep;
+};
+
+// Sums of a, b, c over the block; the totals land in thread 0.
+__device__ void block_sum3(double& a, double& b, double& c, CoopSm& sm) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sm.d0[threadIdx.x >> 5] = a;
+        sm.d1[threadIdx.x >> 5] = b;
+        sm.d2[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = c = 0.0;
+        for (int q = 0; q < QB / 32; ++q) {
+            a += sm.d0[q];
+            b += sm.d1[q];
+            c += sm.d2[q];
+        }
+    }
+    __syncthreads();
+}
+
+// Grid-wide barrier: bar[0] counts arrivals, bar[1] is the generation.  The
+// wait is bounded: after QR_BAR_SPINS polls (or when another block gave up)
+// the block sets *err and the call returns false; the caller returns.
+__device__ bool grid_sync(unsigned* bar, int G, int* err, CoopSm& sm) {
+    __syncthreads();
+    if (G == 1) return true;
+    if (threadIdx.x == 0) {
+        sm.ok = 1;
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();   // this block's writes before its arrival
+        const unsigned a = atomicAdd(bar, 1u);
+        if (a == (unsigned)G - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > QR_BAR_SPINS || *(volatile int*)err) {
+                    atomicExch(err, 1);
+                    sm.ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();   // acquire: the other blocks' writes
+    }
+    __syncthreads();
+    return sm.ok != 0;
+}
+
+// out[e] = sum over the G partial rows part[g * PSTRIDE + e] (in increasing
+// g), e < E, by all threads of the calling block.
+__device__ void sum_rows(const cplx* part, int G, int E, cplx* out, CoopSm& sm) {
+    const int t = threadIdx.x;
+    if (E > QB) {
+        for (int e = t; e < E; e += QB) {
+            cplx s0 = make_double2(0.0, 0.0), s1 = s0;
+            int g = 0;
+#pragma unroll 4
+            for (; g + 1 < G; g += 2) {
+                s0 = cadd(s0, __ldcg(part + (long long)g * PSTRIDE + e));
+                s1 = cadd(s1, __ldcg(part + (long long)(g + 1) * PSTRIDE + e));
+            }
+            if (g < G) s0 = cadd(s0, __ldcg(part + (long long)g * PSTRIDE + e));
+            out[e] = cadd(s0, s1);
+        }
+        __syncthreads();
+        return;
+    }
+    int c = 1;                          // chunks of rows per entry (power of two)
+    while (2 * c * E <= QB) c *= 2;
+    const int L = (G + c - 1) / c;
+    const int e = t / c, q = t % c;
+    cplx s0 = make_double2(0.0, 0.0), s1 = s0;
+    if (e < E) {
+        const int g1 = min(G, (q + 1) * L);
+        int g = q * L;
+#pragma unroll 4
+        for (; g + 1 < g1; g += 2) {
+            s0 = cadd(s0, __ldcg(part + (long long)g * PSTRIDE + e));
+            s1 = cadd(s1, __ldcg(part + (long long)(g + 1) * PSTRIDE + e));
+        }
+        if (g < g1) s0 = cadd(s0, __ldcg(part + (long long)g * PSTRIDE + e));
+    }
+    cplx sv = cadd(s0, s1);
+    const int seg = c < 32 ? c : 32;
+    for (int o = seg / 2; o > 0; o >>= 1) {
+        sv.x += __shfl_xor_sync(0xffffffffu, sv.x, o);
+        sv.y += __shfl_xor_sync(0xffffffffu, sv.y, o);
+    }
+    if (q % 32 == 0) sm.red[t / seg] = sv;
+    __syncthreads();
+    const int per = c / seg;
+    if (t < E) {
+        cplx a = sm.red[t * per];
+        for (int w = 1; w < per; ++w) a = cadd(a, sm.red[t * per + w]);
+        out[t] = a;
+    }
+    __syncthreads();
+}
+
+// Row rr of kept column j (shared-memory cache or global).
+__device__ __forceinline__ cplx qcol(const cplx* A, long long M, long long r0, const cplx* qc, int nc, int j, int rr,
+                                     const CoopSm& sm) {
+    return j < nc ? qc[j * QCS + rr] : A[r0 + rr + (long long)sm.nz[j] * M];
+}
+
+// This block's partials of X(k): out[j] = Q_j^H v1, out[n + j] = Q_j^H a_next
+// (j < n), out[2n] = v1^H a_next, out[2n + 1] = (|v1|^2, fro) over its rows.
+__device__ void coop_partials(const cplx* A, long long M, long long r0, int nrows, int n, const cplx* qc, int nc,
+                              double fro, cplx* out, CoopSm& sm) {
+    const int t = threadIdx.x;
+    if (n > QB) {
+        for (int j = t; j < n; j += QB) {
+            cplx sv = make_double2(0.0, 0.0), sa = sv;
+            for (int rr = 0; rr < nrows; ++rr) {
+                cplx a = qcol(A, M, r0, qc, nc, j, rr, sm), v = sm.v1[rr], b = sm.an[rr];
+                sv.x = fma(a.x, v.x, fma(a.y, v.y, sv.x));
+                sv.y = fma(a.x, v.y, fma(-a.y, v.x, sv.y));
+                sa.x = fma(a.x, b.x, fma(a.y, b.y, sa.x));
+                sa.y = fma(a.x, b.y, fma(-a.y, b.x, sa.y));
+            }
+            out[j] = sv;
+            out[n + j] = sa;
+        }
+    } else if (n > 0) {
+        // sl row slices per column, sl a power of two so that the slices of
+        // one column are reduced by shuffles (within a warp) and at most
+        // four shared-memory terms (across warps)
+        int sl = 1;
+        while (2 * sl * n <= QB) sl *= 2;
+        const int j = t / sl, q = t % sl;
+        cplx sv = make_double2(0.0, 0.0), sa = sv;
+        if (j < n) {
+#pragma unroll 2
+            for (int rr = q; rr < nrows; rr += sl) {
+                cplx a = qcol(A, M, r0, qc, nc, j, rr, sm), v = sm.v1[rr], b = sm.an[rr];
+                sv.x = fma(a.x, v.x, fma(a.y, v.y, sv.x));
+                sv.y = fma(a.x, v.y, fma(-a.y, v.x, sv.y));
+                sa.x = fma(a.x, b.x, fma(a.y, b.y, sa.x));
+                sa.y = fma(a.x, b.y, fma(-a.y, b.x, sa.y));
+            }
+        }
+        const int seg = sl < 32 ? sl : 32;
+        for (int o = seg / 2; o > 0; o >>= 1) {
+            sv.x += __shfl_xor_sync(0xffffffffu, sv.x, o);
+            sv.y += __shfl_xor_sync(0xffffffffu, sv.y, o);
+            sa.x += __shfl_xor_sync(0xffffffffu, sa.x, o);
+            sa.y += __shfl_xor_sync(0xffffffffu, sa.y, o);
+        }
+        if (q % 32 == 0) {
+            sm.red[2 * (t / seg)] = sv;
+            sm.red[2 * (t / seg) + 1] = sa;
+        }
+        __syncthreads();
+        const int per = sl / seg;          // warp partials per column (1 to 4)
+        if (t < n) {
+            cplx a = sm.red[2 * t * per], b = sm.red[2 * t * per + 1];
+            for (int w = 1; w < per; ++w) {
+                a = cadd(a, sm.red[2 * (t * per + w)]);
+                b = cadd(b, sm.red[2 * (t * per + w) + 1]);
+            }
+            out[t] = a;
+            out[n + t] = b;
+        }
+    }
+    double vv = 0.0, cx = 0.0, cy = 0.0;
+    if (t < nrows) {
+        cplx v = sm.v1[t], b = sm.an[t];
+        vv = v.x * v.x + v.y * v.y;
+        cx = v.x * b.x + v.y * b.y;
+        cy = v.x * b.y - v.y * b.x;
+    }
+    block_sum3(vv, cx, cy, sm);
+    if (t == 0) {
+        out[2 * n] = make_double2(cx, cy);
+        out[2 * n + 1] = make_double2(vv, fro);
+    }
+    __syncthreads();
+}
+
+// sum_j Q[r, nz_j] h[j] for this thread's row (j < n).
+__device__ __forceinline__ cplx coop_combo(const cplx* A, long long M, long long r0, int t, const cplx* qc, int nc,
+                                           int n, const cplx* h, const CoopSm& sm) {
+    cplx u0 = make_double2(0.0, 0.0), u1 = u0;
+    int j = 0;
+#pragma unroll 2
+    for (; j + 1 < n; j += 2) {
+        cplx a = qcol(A, M, r0, qc, nc, j, t, sm), b = qcol(A, M, r0, qc, nc, j + 1, t, sm);
+        cplx ha = h[j], hb = h[j + 1];
+        u0.x = fma(a.x, ha.x, fma(-a.y, ha.y, u0.x));
+        u0.y = fma(a.x, ha.y, fma(a.y, ha.x, u0.y));
+        u1.x = fma(b.x, hb.x, fma(-b.y, hb.y, u1.x));
+        u1.y = fma(b.x, hb.y, fma(b.y, hb.x, u1.y));
+    }
+    if (j < n) {
+        cplx a = qcol(A, M, r0, qc, nc, j, t, sm), ha = h[j];
+        u0.x = fma(a.x, ha.x, fma(-a.y, ha.y, u0.x));
+        u0.y = fma(a.x, ha.y, fma(a.y, ha.x, u0.y));
+    }
+    return cadd(u0, u1);
+}
+
+// Sums of the partial rows of one synchronisation into sm.hb (E entries).
+// Few entries: every block sums all rows itself.  Many: block b sums the
+// entries e = b (mod G) into red_out, and a second synchronisation publishes
+// them (so no block reads more than a few rows per thread).
+__device__ bool coop_reduce(const cplx* part, int G, int E, cplx* red_out, unsigned* bar, int* err, CoopSm& sm) {
+    if (G == 1) return true;   // the block wrote its partials to sm.hb
+    if (!grid_sync(bar, G, err, sm)) return false;
+    if ((long long)E * G <= 32LL * QB) {
+        sum_rows(part, G, E, sm.hb, sm);
+        return true;
+    }
+    const int t = threadIdx.x;
+    for (int e = blockIdx.x; e < E; e += G) {
+        cplx s = make_double2(0.0, 0.0);
+        for (int g = t; g < G; g += QB) s = cadd(s, __ldcg(part + (long long)g * PSTRIDE + e));
+        sm.red[t] = s;
+        __syncthreads();
+        for (int w = QB / 2; w > 0; w >>= 1) {
+            if (t < w) sm.red[t] = cadd(sm.red[t], sm.red[t + w]);
+            __syncthreads();
+        }
+        if (t == 0) red_out[e] = sm.red[0];
+        __syncthreads();
+    }
+    if (!grid_sync(bar, G, err, sm)) return false;
+    for (int e = t; e < E; e += QB) sm.hb[e] = __ldcg(red_out + e);
+    __syncthreads();
+    return true;
+}
+
+__global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D, cplx* R, int* flags, cplx* part,
+                                                     cplx* red_out, unsigned* bar, int* err, int nc_max) {
+    extern __shared__ cplx qc[];   // nc_max cached columns of QCS rows
+    __shared__ CoopSm sm;
+    const int G = gridDim.x, t = threadIdx.x;
+    const long long r0 = (long long)blockIdx.x * QB;
+    const int nrows = (int)min((long long)QB, M - r0);
+    const bool own = t < nrows;
+    const long long r = r0 + t;
+    const bool b0 = blockIdx.x == 0;
+
+    // |A|_F^2 over this block's rows; v1_0 = a_0, a_next = a_1
+    double fro = 0.0, dz0 = 0.0, dz1 = 0.0;
+    if (own)
+        for (int j = 0; j < D; ++j) {
+            cplx a = A[r + (long long)j * M];
+            fro += a.x * a.x + a.y * a.y;
+        }
+    block_sum3(fro, dz0, dz1, sm);
+    sm.v1[t] = own ? A[r] : make_double2(0.0, 0.0);
+    sm.an[t] = (own && D > 1) ? A[r + M] : make_double2(0.0, 0.0);
+    if (t == 0) sm.nnz = 0;
+    __syncthreads();
+    for (int k = 0; k < D; ++k) {
+        const int n = sm.nnz, E = 2 * n + 2;
+        const int nc = min(n, nc_max);
+        // prefetch a_{k+2}; its latency hides behind the synchronisation
+        const cplx pre = (own && k + 2 < D) ? A[r + (long long)(k + 2) * M] : make_double2(0.0, 0.0);
+        cplx* prow = part + ((long long)(k & 1) * G + blockIdx.x) * PSTRIDE;
+        coop_partials(A, M, r0, nrows, n, qc, nc, k == 0 ? fro : 0.0, G == 1 ? sm.hb : prow, sm);
+        if (!coop_reduce(part + (long long)(k & 1) * G * PSTRIDE, G, E, red_out, bar, err, sm)) return;
+        // decide column k; first-pass coefficient of a_{k+1} along q_k
+        if (k == 0 && t == 0) sm.fro2 = sm.hb[1].y;
+        __syncthreads();
+        {
+            double s2 = 0.0, px = 0.0, py = 0.0;   // |h2|^2 and h2^H g
+            for (int j = t; j < n; j += QB) {
+                cplx h2 = sm.hb[j], g = sm.hb[n + j];
+                s2 += h2.x * h2.x + h2.y * h2.y;
+                px += h2.x * g.x + h2.y * g.y;
+                py += h2.x * g.y - h2.y * g.x;
+                if (b0) R[(long long)k * D + sm.nz[j]] = cadd(sm.h1s[j], h2);
+            }
+            block_sum3(s2, px, py, sm);
+            if (t == 0) {
+                const double nrm = sqrt(fmax(sm.hb[2 * n + 1].x - s2, 0.0)), f = sqrt(sm.fro2);
+                const int dep = (f == 0.0) || (nrm <= QR_TOL * f);
+                const double sc = dep ? 0.0 : 1.0 / nrm;
+                sm.dep = dep;
+                sm.scale = sc;
+                const cplx c = sm.hb[2 * n];
+                sm.hk = make_double2(sc * (c.x - px), sc * (c.y - py));
+                if (b0) {
+                    R[(long long)k * D + k] = make_double2(dep ? 0.0 : nrm, 0.0);
+                    flags[k] = dep;
+                }
+            }
+            __syncthreads();
+        }
+        // finalise q_k = (v1_k - Q h2) * scale for this block's rows
+        if (own) {
+            cplx w = sm.v1[t], u = coop_combo(A, M, r0, t, qc, nc, n, sm.hb, sm);
+            w = make_double2((w.x - u.x) * sm.scale, (w.y - u.y) * sm.scale);
+            A[r + (long long)k * M] = w;
+            if (!sm.dep && n < nc_max) qc[n * QCS + t] = w;
+        }
+        __syncthreads();
+        if (k + 1 == D) break;
+        // h1_{k+1} = [g ; hk], v1_{k+1} = a_{k+1} - Q h1_{k+1}
+        for (int j = t; j < n; j += QB) sm.h1s[j] = sm.hb[n + j];
+        if (t == 0 && !sm.dep) {
+            sm.h1s[n] = sm.hk;
+            sm.nz[n] = k;
+            sm.nnz = n + 1;
+        }
+        __syncthreads();
+        const int n1 = sm.nnz, nc1 = min(n1, nc_max);
+        if (own) {
+            cplx a = sm.an[t], u = coop_combo(A, M, r0, t, qc, nc1, n1, sm.h1s, sm);
+            sm.v1[t] = make_double2(a.x - u.x, a.y - u.y);
+        }
+        sm.an[t] = pre;
+        __syncthreads();
+    }
 }
 
 // Decide and scale the last column.
@@ -238,14 +626,15 @@ __global__ void __launch_bounds__(QB) rownorm_kernel(const cplx* A, long long M,
     rownorm[r] = s;
 }
 
-// One block: first candidate with 1 - rownorm >= 1/4, else argmax (earliest).
-__global__ void pick_kernel(const double* rownorm, const int* cand, int ncand, int* pick) {
-    __shared__ int sfirst[32];
-    __shared__ double sbest[32];
-    __shared__ int sbi[32];
-    int first = ncand;
+// First candidate with 1 - rownorm >= 1/4, else the largest residual
+// (earliest on ties); computed identically by every block.
+__device__ int pick_candidate(const double* rownorm, const int* cand, int ncand) {
+    __shared__ int sfirst[QB / 32];
+    __shared__ double sbest[QB / 32];
+    __shared__ int sbi[QB / 32];
+    __shared__ int result;
+    int first = ncand, bi = ncand;
     double best = -1.0;
-    int bi = ncand;
     for (int p = threadIdx.x; p < ncand; p += blockDim.x) {
         double res = 1.0 - rownorm[cand[p]];
         if (res >= MIN_RES2 && p < first) first = p;
@@ -264,7 +653,7 @@ __global__ void pick_kernel(const double* rownorm, const int* cand, int ncand, i
             bi = i2;
         }
     }
-    int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         sfirst[w] = first;
         sbest[w] = best;
@@ -274,7 +663,7 @@ __global__ void pick_kernel(const double* rownorm, const int* cand, int ncand, i
     if (threadIdx.x == 0) {
         int f = ncand, b = ncand;
         double bv = -1.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+        for (int i = 0; i < QB / 32; ++i) {
             f = min(f, sfirst[i]);
             if (sbest[i] > bv || (sbest[i] == bv && sbi[i] < b)) {
                 bv = sbest[i];
@@ -282,17 +671,21 @@ __global__ void pick_kernel(const double* rownorm, const int* cand, int ncand, i
             }
         }
         int p = f < ncand ? f : b;
-        pick[0] = (p < ncand) ? cand[p] : 0;
+        result = (p < ncand) ? cand[p] : 0;
     }
+    __syncthreads();
+    return result;
 }
 
-// column k <- e_c - sum_j A_j conj(A(c, j)) over nonzero j; then dots with them
+// column k <- e_c - sum_j A_j conj(A(c, j)) over nonzero j for the picked
+// candidate c; then dots with the nonzero columns
 __global__ void __launch_bounds__(QB) gs_unit_kernel(cplx* A, long long M, int D, int k, const int* flags,
-                                                     const int* pick, cplx* part, int G) {
+                                                     const double* rownorm, const int* cand, int ncand, cplx* part,
+                                                     int G) {
     __shared__ int szero[MAXD];
     __shared__ cplx rowc[MAXD];
     __shared__ cplx wsum[MAXD][QB / 32];
-    const int c = pick[0];
+    const int c = pick_candidate(rownorm, cand, ncand);
     for (int j = threadIdx.x; j < D; j += QB) {
         szero[j] = flags[j] || j == k;
         cplx v = A[c + (long long)j * M];
@@ -349,6 +742,9 @@ __global__ void __launch_bounds__(QB) normalize_col_kernel(cplx* A, long long M,
     if (threadIdx.x == 0) {
         double s = sum_norm(pnorm, G);
         inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+        // the completed column joins Q for later completions (no block of
+        // this kernel reads the flags)
+        if (blockIdx.x == 0) flags[k] = 0;
     }
     __syncthreads();
     long long r = blockIdx.x * (long long)QB + threadIdx.x;
@@ -359,11 +755,6 @@ __global__ void __launch_bounds__(QB) normalize_col_kernel(cplx* A, long long M,
         A[r + (long long)k * M] = v;
         rownorm[r] += v.x * v.x + v.y * v.y;
     }
-}
-
-// the completed column becomes part of Q for later completions
-__global__ void unflag_kernel(int* flags, int k) {
-    if (threadIdx.x == 0) flags[k] = 0;
 }
 
 // ------------------------------------------------ structured completion
@@ -519,30 +910,73 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
     cplx* part1 = ws.part;
     cplx* part2 = ws.part + (size_t)G * (D + 1);
     cudaMemsetAsync(R, 0, sizeof(cplx) * (size_t)D * D, s);
-    int Gf = (int)std::min<long long>((MM * D + 255) / 256, QR_FROB_BLOCKS);
-    frob_partial_kernel<<<Gf, 256, 0, s>>>(A, MM * D, ws.pnorm);
-    frob_finish_kernel<<<1, 32, 0, s>>>(ws.pnorm, Gf, ws.scal);
-    col_norm_kernel<<<G, QB, 0, s>>>(A, MM, ws.pnorm);
-    launches += 3;
-    for (int k = 1; k < D; ++k) {
-        qr_k1<<<G, QB, 0, s>>>(A, MM, D, k, ws.pnorm, G, ws.scal, R, ws.flags, part1);
-        qr_k2<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, ws.scal, part1, part2, R, G);
-        qr_k3<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, part2, R, ws.pnorm, G);
-        launches += 3;
+    // one cooperative launch for the column loop when all G blocks fit on
+    // the GPU at once (with as many cached columns per block as allows);
+    // otherwise three launches per column
+    static int coop_limit[3] = {-1, -1, -1};   // max co-resident blocks at QC_MAX, 8, 0 cached columns
+    static const int nc_opts[3] = {QC_MAX, 8, 0};
+    if (coop_limit[0] < 0) {
+        int dev = 0, nsm = 0, coop = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(cplx) * QC_MAX * QCS));
+        for (int i = 0; i < 3; ++i) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, QB,
+                                                          sizeof(cplx) * nc_opts[i] * QCS);
+            coop_limit[i] = coop ? nsm * per_sm : 0;
+        }
     }
-    qr_last<<<G, QB, 0, s>>>(A, MM, D, ws.pnorm, G, ws.scal, R, ws.flags);
-    launches += 1;
+    bool coop_done = false;
+    for (int i = 0; i < 3 && !coop_done && D <= MAXD; ++i) {
+        if (G > coop_limit[i]) continue;
+        int nc = nc_opts[i];
+        size_t smem = sizeof(cplx) * nc * QCS;
+        // the barrier leaves its arrival count at zero after every completed
+        // wait, so it needs a reset only after an error
+        void* args[] = {(void*)&A, (void*)&MM, (void*)&D, (void*)&R, (void*)&ws.flags, (void*)&ws.part,
+                        (void*)&ws.h, (void*)&ws.bar, (void*)&ws.err, (void*)&nc};
+        coop_done = cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(G), dim3(QB), args, smem, s) ==
+                    cudaSuccess;
+        if (!coop_done) cudaGetLastError();   // clear and use the multi-launch path
+        launches += 1;
+    }
+    if (!coop_done) {
+        int Gf = (int)std::min<long long>((MM * D + 255) / 256, QR_FROB_BLOCKS);
+        frob_partial_kernel<<<Gf, 256, 0, s>>>(A, MM * D, ws.pnorm);
+        frob_finish_kernel<<<1, 32, 0, s>>>(ws.pnorm, Gf, ws.scal);
+        col_norm_kernel<<<G, QB, 0, s>>>(A, MM, ws.pnorm);
+        launches += 3;
+        for (int k = 1; k < D; ++k) {
+            qr_k1<<<G, QB, 0, s>>>(A, MM, D, k, ws.pnorm, G, ws.scal, R, ws.flags, part1);
+            qr_k2<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, ws.scal, part1, part2, R, G);
+            qr_k3<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, part2, R, ws.pnorm, G);
+            launches += 3;
+        }
+        qr_last<<<G, QB, 0, s>>>(A, MM, D, ws.pnorm, G, ws.scal, R, ws.flags);
+        launches += 1;
+    }
 
     // dependent columns -> completion
-    static thread_local int hflags[MAXD];
+    static thread_local int hflags[MAXD], herr;
     cudaMemcpyAsync(hflags, ws.flags, sizeof(int) * D, cudaMemcpyDeviceToHost, s);
+    herr = 0;
+    if (coop_done) cudaMemcpyAsync(&herr, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
+    if (herr) {   // a grid-barrier wait gave up: clear the flag, report
+        cudaMemsetAsync(ws.err, 0, sizeof(int), s);
+        cudaMemsetAsync(ws.bar, 0, 2 * sizeof(unsigned), s);
+        cudaStreamSynchronize(s);
+        return -1;
+    }
     int ndep = 0;
     for (int k = 0; k < D; ++k) ndep += hflags[k] ? 1 : 0;
     if (n_dependent_host) *n_dependent_host = ndep;
     if (ndep == 0) return launches;
     const int r = D - ndep;
-    if (r <= QR_SC_MAXR && MM >= 4LL * D && (size_t)r * ndep * sizeof(cplx) <= 96 * 1024) {
+    if (r <= QR_SC_MAXR && (size_t)r * ndep * sizeof(cplx) <= 96 * 1024) {
         static thread_local int hk[MAXD], hd[MAXD];
         int nk = 0, nd = 0;
         for (int k = 0; k < D; ++k) {
@@ -572,12 +1006,10 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
     launches += 1;
     for (int k = 0; k < D; ++k) {
         if (!hflags[k]) continue;
-        pick_kernel<<<1, 1024, 0, s>>>(ws.rownorm, cand, ncand, ws.pick);
-        gs_unit_kernel<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, ws.pick, part1, G);
+        gs_unit_kernel<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, ws.rownorm, cand, ncand, part1, G);
         gs_second_kernel<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, part1, ws.pnorm, G);
         normalize_col_kernel<<<G, QB, 0, s>>>(A, MM, k, ws.pnorm, G, ws.rownorm, ws.flags);
-        unflag_kernel<<<1, 32, 0, s>>>(ws.flags, k);
-        launches += 5;
+        launches += 3;
     }
     return launches;
 }

@@ -636,7 +636,13 @@ void qr_leg(ttn_ctx* c, int k, int o) {
     auto key = std::make_pair(k, o);
     {
         ProfScope ps(c, PK_QR, 16.0 * (double)M * D * D, 0.0);
-        c->stats[3] += qr_cgs2(A, (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep);
+        int nl = qr_cgs2(A, (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep);
+        if (nl < 0) throw TtnError(TTN_ERR_TIMEOUT, "QR grid barrier wait timed out");
+        c->stats[3] += nl;
+        ps.shape[0] = (int)M;   // profile record: rows, columns, dependent columns
+        ps.shape[1] = D;
+        ps.shape[2] = ndep;
+        ps.shape[3] = 1;
     }
     c->stats[4] += 1;
     c->stats[5] += ndep;
@@ -899,6 +905,29 @@ void build_tree(ttn_ctx* c) {
     }
 }
 
+// QR scratch for matrices of up to maxM rows and maxD columns.
+void alloc_qr_scratch(ttn_ctx* c, long long maxM, int maxD, QrScratch& q) {
+    const long long gq = (maxM + QR_ROWS - 1) / QR_ROWS;   // row blocks
+    q.part = (cplx*)dalloc(c, sizeof(cplx) * 2 * gq * (2 * MAX_CHI + 4));   // two buffers of partial rows
+    q.h = (cplx*)dalloc(c, sizeof(cplx) * 2 * (MAX_CHI + 2));   // two coefficient vectors
+    q.pnorm = (double*)dalloc(c, sizeof(double) * std::max<long long>(gq, QR_FROB_BLOCKS));
+    q.scal = (double*)dalloc(c, sizeof(double) * 8);
+    q.flags = (int*)dalloc(c, sizeof(int) * (maxD + 2));
+    q.rownorm = (double*)dalloc(c, sizeof(double) * std::max<long long>(maxM, 1));
+    q.pick = (int*)dalloc(c, sizeof(int) * 4);
+    q.kept = (int*)dalloc(c, sizeof(int) * (maxD + 2));
+    q.dep = (int*)dalloc(c, sizeof(int) * (maxD + 2));
+    q.acc_rows = (int*)dalloc(c, sizeof(int) * (maxD + 2));
+    q.Y = (cplx*)dalloc(c, sizeof(cplx) * QR_SC_MAXR * (maxD + 2));
+    q.nu = (double*)dalloc(c, sizeof(double) * (maxD + 2));
+    q.row_rank = (int*)dalloc(c, sizeof(int) * std::max<long long>(maxM, 1));
+    q.cand_used = (int*)dalloc(c, sizeof(int) * std::max<long long>(maxM, 1));
+    q.bar = (unsigned*)dalloc(c, sizeof(unsigned) * 4);
+    q.err = (int*)dalloc(c, sizeof(int) * 4);
+    CUDA_OK(cudaMemset(q.err, 0, sizeof(int) * 4));
+    CUDA_OK(cudaMemset(q.bar, 0, sizeof(unsigned) * 4));
+}
+
 void allocate(ttn_ctx* c) {
     int nn = (int)c->nodes.size();
     c->T.assign(nn, nullptr);
@@ -930,24 +959,10 @@ void allocate(ttn_ctx* c) {
     c->kh2 = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1));
     c->kpart = (cplx*)dalloc(c, sizeof(cplx) * 2 * RED_BLOCKS * (MAX_CHI + 2));
     c->kpn = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
-    long long gq = 1;   // QR row blocks: max over nodes and legs of ceil((s / d_leg) / QR_ROWS)
+    long long mq = 1;   // largest QR row count: max over nodes and legs of s / d_leg
     for (int k = 0; k < nn; ++k)
-        for (int u = 0; u < 3; ++u)
-            gq = std::max(gq, (c->nodes[k].s / c->nodes[k].d[u] + QR_ROWS - 1) / QR_ROWS);
-    c->qr.part = (cplx*)dalloc(c, sizeof(cplx) * 2 * gq * (MAX_CHI + 2));
-    c->qr.h = (cplx*)dalloc(c, sizeof(cplx) * (MAX_CHI + 2));
-    c->qr.pnorm = (double*)dalloc(c, sizeof(double) * std::max<long long>(gq, QR_FROB_BLOCKS));
-    c->qr.scal = (double*)dalloc(c, sizeof(double) * 8);
-    c->qr.flags = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
-    c->qr.rownorm = (double*)dalloc(c, sizeof(double) * c->smax);
-    c->qr.pick = (int*)dalloc(c, sizeof(int) * 4);
-    c->qr.kept = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
-    c->qr.dep = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
-    c->qr.acc_rows = (int*)dalloc(c, sizeof(int) * (MAX_CHI + 2));
-    c->qr.Y = (cplx*)dalloc(c, sizeof(cplx) * QR_SC_MAXR * (MAX_CHI + 2));
-    c->qr.nu = (double*)dalloc(c, sizeof(double) * (MAX_CHI + 2));
-    c->qr.row_rank = (int*)dalloc(c, sizeof(int) * c->smax);
-    c->qr.cand_used = (int*)dalloc(c, sizeof(int) * c->smax);
+        for (int u = 0; u < 3; ++u) mq = std::max(mq, c->nodes[k].s / c->nodes[k].d[u]);
+    alloc_qr_scratch(c, mq, MAX_CHI, c->qr);
     c->d_coef = (double*)dalloc(c, sizeof(double) * 5 * c->N);
     c->h_coef.assign(5 * c->N, 0.0);
     CUDA_OK(cudaMallocHost(&c->hflag, 4 * sizeof(int)));
@@ -999,7 +1014,8 @@ void build_from_branches(ttn_ctx* c, const std::vector<std::vector<zc>>& leaf_br
             CUDA_OK(cudaMemcpy(c->T[k], A.data(), sizeof(cplx) * M * D, cudaMemcpyHostToDevice));
             int ndep = 0;
             auto key = std::make_pair(k, 2);
-            qr_cgs2(c->T[k], (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep);
+            if (qr_cgs2(c->T[k], (int)M, D, c->Rbuf, c->cand[key], c->ncand[key], c->qr, c->stream, &ndep) < 0)
+                throw TtnError(TTN_ERR_TIMEOUT, "QR grid barrier wait timed out");
             std::vector<zc> R((size_t)D * D), Q(M * D);
             CUDA_OK(cudaMemcpyAsync(R.data(), c->Rbuf, sizeof(cplx) * D * D, cudaMemcpyDeviceToHost, c->stream));
             CUDA_OK(cudaMemcpyAsync(Q.data(), c->T[k], sizeof(cplx) * M * D, cudaMemcpyDeviceToHost, c->stream));
@@ -1723,6 +1739,54 @@ ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned lo
         tmp.allocs.clear();
         if (tmp.split_ws) cudaFree(tmp.split_ws);
         tmp.split_ws = nullptr;
+    });
+}
+
+ttn_status ttn_selftest_qr(const double* A, int M, int D, const int* cand, int ncand, double* Q, double* R,
+                          int* n_dependent, float* ms) {
+    if (M < 1 || D < 1 || D > MAX_CHI || M < D || (long long)M * D > (1LL << 26) || !A || !Q || !R ||
+        (cand && (ncand < 1 || ncand > M)))
+        return TTN_ERR_ARG;
+    if (cand)
+        for (int i = 0; i < ncand; ++i)
+            if (cand[i] < 0 || cand[i] >= M) return TTN_ERR_ARG;
+    ttn_ctx tmp;
+    return guard(&tmp, [&] {
+        struct Free {
+            ttn_ctx* t;
+            ~Free() {
+                for (void* p : t->allocs) cudaFree(p);
+                t->allocs.clear();
+            }
+        } fr{&tmp};
+        QrScratch q;
+        alloc_qr_scratch(&tmp, M, D, q);
+        cplx* dA = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)M * D);
+        cplx* dR = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)D * D);
+        const int nc = cand ? ncand : M;
+        int* dc = (int*)dalloc(&tmp, sizeof(int) * nc);
+        std::vector<int> hc(nc);
+        for (int i = 0; i < nc; ++i) hc[i] = cand ? cand[i] : i;
+        CUDA_OK(cudaMemcpy(dc, hc.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(dA, A, sizeof(cplx) * (size_t)M * D, cudaMemcpyHostToDevice));
+        cudaEvent_t e0, e1;
+        CUDA_OK(cudaEventCreate(&e0));
+        CUDA_OK(cudaEventCreate(&e1));
+        int ndep = 0;
+        CUDA_OK(cudaEventRecord(e0, nullptr));
+        int nl = qr_cgs2(dA, M, D, dR, dc, nc, q, nullptr, &ndep);
+        CUDA_OK(cudaEventRecord(e1, nullptr));
+        CUDA_OK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (nl < 0) throw TtnError(TTN_ERR_TIMEOUT, "QR grid barrier wait timed out");
+        CUDA_OK(cudaGetLastError());
+        CUDA_OK(cudaMemcpy(Q, dA, sizeof(cplx) * (size_t)M * D, cudaMemcpyDeviceToHost));
+        CUDA_OK(cudaMemcpy(R, dR, sizeof(cplx) * (size_t)D * D, cudaMemcpyDeviceToHost));
+        if (n_dependent) *n_dependent = ndep;
+        if (ms) *ms = t;
     });
 }
 

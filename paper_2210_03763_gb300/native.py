@@ -55,6 +55,8 @@ SIGNATURES = [
     ("ttn_selftest_contract", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_ulonglong, ctypes.c_int, _D]),
     ("ttn_profile_end", ctypes.c_int, [_P, _D, ctypes.c_int]),
+    ("ttn_selftest_qr", ctypes.c_int, [_D, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int, _D, _D, _I,
+                                       ctypes.POINTER(ctypes.c_float)]),
     ("ttn_profile_records", ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
     ("ttn_reset_stats", ctypes.c_int, [_P]),
     ("ttn_contract_split_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
@@ -88,6 +90,28 @@ def selftest_contract(M, N, K, precision, seed=1, tf32_exact=False):
     if st != 0:
         raise TTNError(st, "selftest_contract")
     return float(out[0])
+
+
+def selftest_qr(A, cand=None):
+    """GPU QR with deterministic completion of a host complex M x D matrix:
+    returns (Q, R, n_dependent, device ms)."""
+    lib = load()
+    A = np.asfortranarray(np.asarray(A, dtype=np.complex128))
+    M, D = A.shape
+    Q = np.zeros((M, D), dtype=np.complex128, order="F")
+    R = np.zeros((D, D), dtype=np.complex128, order="F")
+    nd = ctypes.c_int(0)
+    ms = ctypes.c_float(0.0)
+    if cand is None:
+        cp, nc = None, 0
+    else:
+        ca = np.ascontiguousarray(cand, dtype=np.int32)
+        cp, nc = ca.ctypes.data_as(_I), len(ca)
+    st = lib.ttn_selftest_qr(A.ctypes.data_as(_D), M, D, cp, nc, Q.ctypes.data_as(_D), R.ctypes.data_as(_D),
+                             ctypes.byref(nd), ctypes.byref(ms))
+    if st != 0:
+        raise TTNError(st, "selftest_qr(%d, %d)" % (M, D))
+    return Q, R, nd.value, ms.value
 
 
 def contract_split_noalloc(A_ptr, B_ptr, C_ptr, M, N, K, stream=None):
