@@ -229,7 +229,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-out", default=None, help="write the kernel profile JSON here")
+    ap.add_argument("--lattice", default=None, help="LXxLY of a smaller case (profiling); default 8x8")
+    ap.add_argument("--chi", type=int, default=None, help="bond dimension of a smaller case; default 128")
     args = ap.parse_args()
+    global LX, LY, CHI, WORKLOAD
+    if args.lattice or args.chi:
+        if args.lattice:
+            LX, LY = (int(v) for v in args.lattice.lower().split("x"))
+        if args.chi:
+            CHI = args.chi
+        WORKLOAD = "%dx%d Rydberg lattice, chi=%d (smaller case of the same workload recipe)" % (LX, LY, CHI)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -302,7 +311,7 @@ def main():
               "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "f64 state, 3xtf32 contractions",
               "data": "synthetic",
-              "config": {"workload": WORKLOAD, "lattice": "8x8", "chi": CHI, "dt": DT,
+              "config": {"workload": WORKLOAD, "lattice": "%dx%d" % (LX, LY), "chi": CHI, "dt": DT,
                          "parallelism": "replicas" if world > 1 else "single",
                          "l2": "working set (node tensors, environments, Krylov basis) > 129 MB L2",
                          "device_mem_gb": round((free0 - free1) / 1e9, 2)},
@@ -339,7 +348,10 @@ def main():
                                   "sample": note}
     if args.profile_out and rank == 0:
         with open(args.profile_out, "w") as fo:
-            json.dump({"prof": prof, "stats": stats}, fo, indent=1)
+            json.dump({"prof": prof, "stats": stats,
+                       "records": {"columns": ["kind", "M", "N", "K", "batches", "ms", "flops"],
+                                   "kinds": ["tc_gemm", "split_pack", "f64_gemm", "qr"],
+                                   "rows": g.profile_records().tolist()}}, fo)
     g.close()
     if dist:
         dist.barrier()

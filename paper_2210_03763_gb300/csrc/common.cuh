@@ -28,9 +28,15 @@ int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream);
 // The workspace's first int is an error flag a timed-out wait sets.
 int launch_zgemm_split(const GemmArgs& g, cudaStream_t stream, void* workspace,
                        size_t workspace_bytes);
-size_t split_workspace_bytes(const GemmArgs& g);
-int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes);
-int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes);
+// max_split caps split-K (K ranges per output tile, used when the tiles
+// cannot fill the GPU; partial sums then live in the workspace and a second
+// kernel adds them in fixed order).  1 disables it.
+constexpr int SPLIT_K_MAX = 1 << 20;
+size_t split_workspace_bytes(const GemmArgs& g, int max_split = SPLIT_K_MAX);
+int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes,
+                      int max_split = SPLIT_K_MAX);
+int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes,
+                     int max_split = SPLIT_K_MAX);
 
 // ---- Lanczos / vector kernels (kernels.cu) --------------------------------
 // Fixed partial-sum grid for reductions: deterministic order, no atomics.

@@ -41,7 +41,8 @@ constexpr int A_TILE = BM * BK * 4;          // 16 KB per plane tile of P
 constexpr int B_TILE = BN * BK * 4;          // 8 KB per plane tile of Q
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr long long SPIN_LIMIT = 1LL << 24;
+constexpr long long SPIN_LIMIT = 1LL << 30;                  // iteration cap behind the time limit
+constexpr unsigned long long WAIT_NS = 2000000000ull;        // 2 s per pipeline wait
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -67,12 +68,39 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity
     return ok;
 }
 
-// Bounded wait: false (and the error flag set) if the phase never completes.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for a pipeline stage.  Returns false when the phase has not
+// completed after WAIT_NS (the error flag is then set) or as soon as another
+// role of this launch, or an earlier launch, has set the flag: one stuck
+// stage ends the whole launch within about WAIT_NS instead of every waiter
+// timing out in turn.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-    for (long long i = 0; i < SPIN_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1; i < SPIN_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            if (*(volatile int*)err) return false;
+            if (global_ns() - t0 > WAIT_NS) break;
+        }
+    }
     atomicExch(err, 1);
     return false;
+}
+
+// Bounded wait that ignores the error flag: used after an abort, to let this
+// CTA's own copies and MMAs in flight finish before it frees TMEM and exits.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0; i < SPIN_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return;
+        if ((i & 63) == 63 && global_ns() - t0 > WAIT_NS) return;
+    }
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -260,6 +288,9 @@ struct EpiArgs {
     cplx alpha, beta;
     int mode;             // 0: alpha = 1, beta = 0; 1: alpha = 1, beta = 1; 2: general
     int* err;
+    int nsplit;           // K ranges per output tile (split-K); > 1: partial results go to W
+    int cps;              // chunks per K range
+    cplx* W;              // nsplit x batches x N x M partial results (column-major per batch)
 };
 
 // double(f) built from f's bits with integer operations (GB300's FP64 pipe is
@@ -293,11 +324,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;      // [NBUF] chunk accumulated in TMEM buffer b
     uint64_t* tempty = tfull + NBUF;       // [NBUF] buffer b drained
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + NBUF);
+    uint64_t* mdone = tempty + NBUF;       // all MMAs of this CTA complete
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+
+    // an earlier launch on this workspace gave up: do nothing (the host
+    // reports the error at its next check)
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = *(volatile int*)ea.err;
+    __syncthreads();
+    if (s_skip) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nchunk = (ea.nkb + CHUNK_KB - 1) / CHUNK_KB;
-    const long long ntiles = (long long)ea.batches * ea.n_qtiles * ea.n_ptiles;
+    const long long ntiles = (long long)ea.nsplit * ea.batches * ea.n_qtiles * ea.n_ptiles;
+    // work item t: P tile fastest, then Q tile, batch, K range; its chunks [c0, c1)
+    auto krange = [&](long long t, int& c0, int& c1) {
+        const int ks = (int)(t / ((long long)ea.batches * ea.n_qtiles * ea.n_ptiles));
+        c0 = ks * ea.cps;
+        c1 = min(nchunk, c0 + ea.cps);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -308,6 +353,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], DRAIN_THREADS);
         }
+        mbar_init(mdone, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -328,9 +374,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const int pt = (int)(t % ea.n_ptiles);
                 const long long rest = t / ea.n_ptiles;
-                const int qt = (int)(rest % ea.n_qtiles), b = (int)(rest / ea.n_qtiles);
+                const int qt = (int)(rest % ea.n_qtiles), b = (int)((rest / ea.n_qtiles) % ea.batches);
                 const int prow0 = b * ea.Pp + pt * BM, qrow0 = b * ea.Qp + qt * BN;
-                for (int kb = 0; kb < ea.nkb; ++kb, ++it) {
+                int c0, c1;
+                krange(t, c0, c1);
+                const int kb1 = min(ea.nkb, c1 * CHUNK_KB);
+                for (int kb = c0 * CHUNK_KB; kb < kb1; ++kb, ++it) {
                     const unsigned s = it % STAGES, round = it / STAGES;
                     if (it >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1, ea.err)) {
                         ok = false;
@@ -344,6 +393,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     tma_load_2d(st + 2 * A_TILE + B_TILE, &mQl, &full[s], kb * BK, qrow0);
                 }
             }
+            // loads of the last STAGES iterations may still be landing if the
+            // MMA issuer stopped early: wait for them before the CTA exits
+            // (immediate when they were consumed)
+            for (unsigned i = it > STAGES ? it - STAGES : 0; i < it; ++i)
+                mbar_drain(&full[i % STAGES], (i / STAGES) & 1);
         }
         __syncwarp();
     } else if (warp == MMA_WARP) {
@@ -351,7 +405,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             unsigned it = 0, cg = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                for (int c = 0; c < nchunk && ok; ++c, ++cg) {
+                int c0, c1;
+                krange(t, c0, c1);
+                for (int c = c0; c < c1 && ok; ++c, ++cg) {
                     const unsigned buf = cg % NBUF;
                     const uint32_t dt = tmem + (uint32_t)(buf * BN);
                     if (cg >= NBUF && !mbar_wait(&tempty[buf], ((cg / NBUF) - 1) & 1, ea.err)) {
@@ -383,6 +439,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     mma_commit(&tfull[buf]);
                 }
             }
+            mma_commit(mdone);   // completes once every MMA issued above has
+            mbar_drain(mdone, 0);
         }
         __syncwarp();
     } else {
@@ -394,14 +452,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int pt = (int)(t % ea.n_ptiles);
             const long long rest = t / ea.n_ptiles;
-            const int qt = (int)(rest % ea.n_qtiles), b = (int)(rest / ea.n_qtiles);
+            const int qt = (int)(rest % ea.n_qtiles), b = (int)((rest / ea.n_qtiles) % ea.batches);
+            const int ks = (int)(rest / ea.n_qtiles / ea.batches);
+            int c0, c1;
+            krange(t, c0, c1);
             float hi[DCOLS], lo[DCOLS];
 #pragma unroll
             for (int j = 0; j < DCOLS; ++j) {
                 hi[j] = 0.f;
                 lo[j] = 0.f;
             }
-            for (int c = 0; c < nchunk; ++c, ++cg) {
+            for (int c = c0; c < c1; ++c, ++cg) {
                 const unsigned buf = cg % NBUF;
                 if (!mbar_wait(&tfull[buf], (cg / NBUF) & 1, ea.err)) {
                     ok = false;
@@ -424,6 +485,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const int pr = prow >> 1;                           // complex row of P
             const int bi = b % ea.Bi, bo = b / ea.Bi;
             cplx* C = ea.C + bi * ea.c_bi + bo * ea.c_bo;
+            // split-K: this K range's partial sum, dense column-major, plain store
+            cplx* Wt = ea.nsplit > 1 ? ea.W + ((long long)ks * ea.batches + b) * ea.M * (long long)ea.N : nullptr;
 #pragma unroll
             for (int j = 0; j < DCOLS; ++j) {
                 double val = f32_to_f64(hi[j]) + f32_to_f64(lo[j]);
@@ -434,6 +497,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 int n = ea.swapped ? pr : qn;
                 if (m >= ea.M || n >= ea.N) continue;
                 double re = val, im = other;
+                if (Wt) {
+                    Wt[m + (long long)n * ea.M] = make_double2(re, im);
+                    continue;
+                }
                 cplx* cp = C + m * ea.c_m + n * ea.c_n;
                 cplx r;
                 if (ea.mode == 0) {                 // alpha = 1, beta = 0
@@ -462,7 +529,53 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
 }
 
+// C = alpha sum_ks W[ks] + beta C, summing the K ranges in increasing order.
+__global__ void splitk_reduce_kernel(EpiArgs ea) {
+    const long long MN = (long long)ea.M * ea.N, total = MN * ea.batches;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / MN);
+        const long long mn = e - b * MN;
+        const int m = (int)(mn % ea.M), n = (int)(mn / ea.M);
+        cplx acc = ea.W[(long long)b * MN + mn];
+        for (int ks = 1; ks < ea.nsplit; ++ks) {
+            cplx w = ea.W[((long long)ks * ea.batches + b) * MN + mn];
+            acc.x += w.x;
+            acc.y += w.y;
+        }
+        const int bi = b % ea.Bi, bo = b / ea.Bi;
+        cplx* cp = ea.C + bi * ea.c_bi + bo * ea.c_bo + m * ea.c_m + n * ea.c_n;
+        cplx r;
+        if (ea.mode == 0) {
+            r = acc;
+        } else if (ea.mode == 1) {
+            cplx o = *cp;
+            r = make_double2(o.x + acc.x, o.y + acc.y);
+        } else {
+            r.x = ea.alpha.x * acc.x - ea.alpha.y * acc.y;
+            r.y = ea.alpha.x * acc.y + ea.alpha.y * acc.x;
+            if (ea.beta.x != 0.0 || ea.beta.y != 0.0) {
+                cplx o = *cp;
+                r.x += ea.beta.x * o.x - ea.beta.y * o.y;
+                r.y += ea.beta.x * o.y + ea.beta.y * o.x;
+            }
+        }
+        *cp = r;
+    }
+}
+
 // ------------------------------------------------------------------- host
+int num_sms() {
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    return n_sm;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -499,10 +612,16 @@ struct Plan {
     int Rp_rows = 0, Rq_rows = 0;    // complex rows of P and Q
     int Pp = 0, Qp = 0, Kp = 0;      // padded real rows / K'
     long long batches = 0;
+    int nsplit = 1, cps = 0;         // split-K: K ranges per tile, chunks per range
+    size_t w_off = 0;                // byte offset of the partial results
     size_t bytes = 0;
 };
 
-Plan plan_for(const GemmArgs& g) {
+// Split-K when the output tiles cannot fill the GPU: K ranges of at least
+// SPLIT_MIN_CHUNKS chunks, as many as keep every SM busy.
+constexpr int SPLIT_MIN_CHUNKS = 4;
+
+Plan plan_for(const GemmArgs& g, int max_split) {
     Plan pl;
     long long K = (long long)g.Ki * g.Ko;
     if (g.M <= 0 || g.N <= 0 || K < 16) return pl;
@@ -522,22 +641,39 @@ Plan plan_for(const GemmArgs& g) {
     size_t pe = (size_t)(pl.p_bcast ? 1 : pl.batches) * pl.Pp * pl.Kp;
     size_t qe = (size_t)(pl.q_bcast ? 1 : pl.batches) * pl.Qp * pl.Kp;
     pl.bytes = 2 * (pe + qe) * sizeof(float) + 256;
+    const int nchunk = (pl.Kp / BK + CHUNK_KB - 1) / CHUNK_KB;
+    const long long tiles = (long long)(pl.Pp / BM) * (pl.Qp / BN) * pl.batches;
+    int ns = 1;
+    if (max_split > 1 && tiles < num_sms())
+        ns = (int)std::min(std::min((long long)max_split, (long long)num_sms() / tiles),
+                           (long long)(nchunk / SPLIT_MIN_CHUNKS));
+    if (ns > 1) {
+        pl.cps = (nchunk + ns - 1) / ns;
+        pl.nsplit = (nchunk + pl.cps - 1) / pl.cps;
+    }
+    if (pl.nsplit > 1) {
+        pl.w_off = (pl.bytes + 255) / 256 * 256;
+        pl.bytes = pl.w_off + (size_t)pl.nsplit * pl.batches * g.M * (size_t)g.N * sizeof(cplx);
+    } else {
+        pl.cps = nchunk;
+    }
     pl.ok = true;
     return pl;
 }
 
 }  // namespace
 
-size_t split_workspace_bytes(const GemmArgs& g) {
-    Plan pl = plan_for(g);
+size_t split_workspace_bytes(const GemmArgs& g, int max_split) {
+    Plan pl = plan_for(g, max_split);
     return pl.ok ? pl.bytes : 0;
 }
 
 // Phase 1 of a split contraction: pack both operands.  Returns kernels
 // launched, -1 if the shape is not handled here (caller uses FP64), -2 if the
 // workspace is too small.
-int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes) {
-    Plan pl = plan_for(g);
+int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes,
+                      int max_split) {
+    Plan pl = plan_for(g, max_split);
     if (!pl.ok || !encode_fn()) return -1;
     if (!workspace || workspace_bytes < pl.bytes) return -2;
     const long long np_b = pl.p_bcast ? 1 : pl.batches, nq_b = pl.q_bcast ? 1 : pl.batches;
@@ -574,8 +710,9 @@ int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, s
 }
 
 // Phase 2: the tcgen05 GEMM on the packed operands of the same GemmArgs.
-int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes) {
-    Plan pl = plan_for(g);
+int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes,
+                     int max_split) {
+    Plan pl = plan_for(g, max_split);
     if (!pl.ok || !workspace || workspace_bytes < pl.bytes) return -1;
     static bool attr_set = false;
     if (!attr_set) {
@@ -604,22 +741,22 @@ int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, si
     const bool a1 = g.alpha.x == 1.0 && g.alpha.y == 0.0;
     ea.mode = (a1 && g.beta.x == 0.0 && g.beta.y == 0.0) ? 0 : (a1 && g.beta.x == 1.0 && g.beta.y == 0.0) ? 1 : 2;
     ea.err = err;
+    ea.nsplit = pl.nsplit;
+    ea.cps = pl.cps;
+    ea.W = pl.nsplit > 1 ? reinterpret_cast<cplx*>(reinterpret_cast<uint8_t*>(workspace) + pl.w_off) : nullptr;
     // persistent: one CTA per SM walks the tiles, P tiles fastest so CTAs
     // sharing a Q tile run together and hit it in L2
     ea.n_ptiles = pl.Pp / BM;
     ea.n_qtiles = pl.Qp / BN;
     ea.batches = (int)pl.batches;
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (n_sm <= 0) n_sm = 1;
-    }
-    long long ntiles = (long long)ea.n_ptiles * ea.n_qtiles * pl.batches;
-    unsigned grid = (unsigned)std::min<long long>(ntiles, n_sm);
+    long long ntiles = (long long)ea.n_ptiles * ea.n_qtiles * pl.batches * pl.nsplit;
+    unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms());
     tc_gemm_kernel<<<grid, GEMM_THREADS, SMEM_BYTES, stream>>>(mPh, mPl, mQh, mQl, ea);
-    return 1;
+    if (pl.nsplit == 1) return 1;
+    long long total = (long long)g.M * g.N * pl.batches;
+    unsigned rg = (unsigned)std::min<long long>((total + 255) / 256, (long long)num_sms() * 8);
+    splitk_reduce_kernel<<<rg, 256, 0, stream>>>(ea);
+    return 2;
 }
 
 int launch_zgemm_split(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes) {

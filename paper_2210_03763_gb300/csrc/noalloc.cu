@@ -52,7 +52,7 @@ extern "C" ttn_status ttn_contract_split_noalloc(const double* A, const double* 
     g.alpha = make_double2(1.0, 0.0);
     g.beta = make_double2(0.0, 0.0);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    size_t need = split_workspace_bytes(g);
+    size_t need = split_workspace_bytes(g, 1);   // no split-K: the scratch size rule stays as documented
     if (need > NOALLOC_SCRATCH_BYTES) return TTN_ERR_ARG;   // beyond the fixed scratch
     if (need == 0) {
         // too small for the tensor-core tiles: the FP64 kernel needs no scratch
@@ -64,7 +64,7 @@ extern "C" ttn_status ttn_contract_split_noalloc(const double* A, const double* 
     if (st != TTN_OK) return st;
     // the error flag at the start of the scratch must start at zero
     if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess) return TTN_ERR_CUDA;
-    if (launch_split_pack(g, s, scratch, NOALLOC_SCRATCH_BYTES) < 0) return TTN_ERR_ARG;
-    if (launch_split_mma(g, s, scratch, NOALLOC_SCRATCH_BYTES) < 0) return TTN_ERR_CUDA;
+    if (launch_split_pack(g, s, scratch, NOALLOC_SCRATCH_BYTES, 1) < 0) return TTN_ERR_ARG;
+    if (launch_split_mma(g, s, scratch, NOALLOC_SCRATCH_BYTES, 1) < 0) return TTN_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ERR_CUDA;
 }

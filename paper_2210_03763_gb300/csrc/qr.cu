@@ -250,7 +250,14 @@ __global__ void __launch_bounds__(QB) qr_k3(cplx* A, long long M, int D, int k, 
 // of column k+1 sharing one reduction.  Only kept columns take part, so a
 // low-rank matrix costs O(M D rank) flops; the first QC_MAX kept columns of a
 // block's rows stay in shared memory.
-constexpr long long QR_BAR_SPINS = 1LL << 22;
+constexpr long long QR_BAR_SPINS = 1LL << 26;              // iteration cap behind the time limit
+constexpr unsigned long long QR_BAR_NS = 2000000000ull;    // 2 s per synchronisation
+
+__device__ __forceinline__ unsigned long long qr_global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 constexpr int QCS = QB + 1;            // cache column stride (odd: no bank conflicts)
 constexpr int QC_MAX = 32;             // kept columns cached in shared memory
 constexpr int PSTRIDE = 2 * MAXD + 4;  // partial row length
@@ -310,8 +317,10 @@ __device__ bool grid_sync(unsigned* bar, int G, int* err, CoopSm& sm) {
             atomicAdd(bar + 1, 1u);
         } else {
             long long spins = 0;
+            const unsigned long long t0 = qr_global_ns();
             while (*vgen == gen) {
-                if (++spins > QR_BAR_SPINS || *(volatile int*)err) {
+                if (++spins > QR_BAR_SPINS || *(volatile int*)err ||
+                    ((spins & 63) == 0 && qr_global_ns() - t0 > QR_BAR_NS)) {
                     atomicExch(err, 1);
                     sm.ok = 0;
                     break;

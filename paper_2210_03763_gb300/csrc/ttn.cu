@@ -290,7 +290,11 @@ void check_split_flag(ttn_ctx* c) {
     int flag = 0;
     CUDA_OK(cudaMemcpyAsync(&flag, c->split_ws, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_OK(cudaStreamSynchronize(c->stream));
-    if (flag) throw TtnError(TTN_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
+    if (flag) {   // clear it so that the context can be used again once its state is reloaded
+        const int zero = 0;
+        CUDA_OK(cudaMemcpy(c->split_ws, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        throw TtnError(TTN_ERR_TIMEOUT, "tensor-core GEMM pipeline wait timed out");
+    }
 }
 
 GemmArgs base_args() {

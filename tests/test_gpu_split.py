@@ -19,7 +19,9 @@ HEFF_TOL = 6e-6
 
 
 @pytest.mark.parametrize("M,N,K", [(64, 64, 16), (128, 128, 128), (128, 16384, 2048), (16384, 128, 128),
-                                   (200, 70, 33)])
+                                   (200, 70, 33),
+                                   # few output tiles, long K: split-K with partial sums added in FP64
+                                   (128, 128, 16384), (81, 81, 10368), (100, 90, 5003)])
 @pytest.mark.parametrize("tf32_exact", [False, True])
 def test_split_contraction_vs_fp64_kernel(native, M, N, K, tf32_exact):
     err = native.selftest_contract(M, N, K, native.SPLIT_TF32X3, seed=3, tf32_exact=tf32_exact)
