@@ -45,6 +45,21 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def tc_traffic():
+    """DRAM bytes per tc_gemm launch from the committed ncu summary, or None
+    when the kernel source has changed since those counters were taken."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "tc_gemm_8x8_chi128_slice.md")).read()
+        kv = dict(l.strip().split(": ", 1) for l in txt.splitlines() if l.startswith("    ") and ": " in l)
+        src = open(os.path.join(ROOT, kv["kernel_source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != kv["kernel_source_sha256_prefix"]:
+            return None
+        return float(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def workload():
     from paper_2210_03763_gb300 import workloads as W
     xy = W.square_lattice(LX, LY)
@@ -303,7 +318,9 @@ def main():
         roof = {"bound": "tensor", "kernel": "tc_gemm_kernel (tcgen05 kind::tf32, 3xTF32)",
                 "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
                 "peak_source": "%s bf16 burst x 1.1/2.25 (nominal TF32:BF16)" % peak_kind,
-                "traffic": None, "launches": tc["launches"],
+                "traffic": tc_traffic(), "launches": tc["launches"],
+                "traffic_source": "ncu dram__bytes_read+write per launch, mean over the first 150 tc_gemm "
+                                  "launches of one 8x8 chi=128 step (profiles/tc_gemm_8x8_chi128_slice.md)",
                 "share_of_step": tc["ms"] / (secs * 1e3),
                 "flops_counted": "algorithmic 8*M*N*K per complex contraction; tensor pipe executes 3x"}
 

@@ -617,9 +617,13 @@ struct Plan {
     size_t bytes = 0;
 };
 
-// Split-K when the output tiles cannot fill the GPU: K ranges of at least
-// SPLIT_MIN_CHUNKS chunks, as many as keep every SM busy.
+// Split-K: the number of K ranges that minimises the modelled makespan,
+// waves x (chunks per range + SPLIT_EPI_CHUNKS), where a wave is one work
+// item per SM and SPLIT_EPI_CHUNKS charges each work item's epilogue in
+// units of chunks; ranges have at least SPLIT_MIN_CHUNKS chunks.  A split
+// must beat the unsplit plan by 3% to be taken.
 constexpr int SPLIT_MIN_CHUNKS = 4;
+constexpr int SPLIT_EPI_CHUNKS = 4;
 
 Plan plan_for(const GemmArgs& g, int max_split) {
     Plan pl;
@@ -644,9 +648,20 @@ Plan plan_for(const GemmArgs& g, int max_split) {
     const int nchunk = (pl.Kp / BK + CHUNK_KB - 1) / CHUNK_KB;
     const long long tiles = (long long)(pl.Pp / BM) * (pl.Qp / BN) * pl.batches;
     int ns = 1;
-    if (max_split > 1 && tiles < num_sms())
-        ns = (int)std::min(std::min((long long)max_split, (long long)num_sms() / tiles),
-                           (long long)(nchunk / SPLIT_MIN_CHUNKS));
+    if (max_split > 1) {
+        const long long sms = num_sms();
+        auto cost = [&](int n) {
+            const int c = (nchunk + n - 1) / n, k = (nchunk + c - 1) / c;
+            return (double)((tiles * k + sms - 1) / sms) * (c + SPLIT_EPI_CHUNKS);
+        };
+        double best = 0.97 * cost(1);
+        const int lim = std::min(std::min(max_split, nchunk / SPLIT_MIN_CHUNKS), 256);
+        for (int n = 2; n <= lim; ++n)
+            if (cost(n) < best) {
+                best = cost(n);
+                ns = n;
+            }
+    }
     if (ns > 1) {
         pl.cps = (nchunk + ns - 1) / ns;
         pl.nsplit = (nchunk + pl.cps - 1) / pl.cps;
