@@ -517,10 +517,92 @@ __device__ bool coop_reduce(const cplx* part, int G, int E, cplx* red_out, unsig
     return true;
 }
 
+// ---------------------------------------------- look-ahead over dependent runs
+// After a dependent column the kept set Q often stays the same for many
+// columns (low-rank node tensors).  A window of the next W columns then takes
+// both Gram-Schmidt passes against Q together, in two synchronisations:
+//   L1: g_j = Q^H a_j                         v1_j = a_j - Q g_j
+//   L2: h2_j = Q^H v1_j, |v1_j|^2, v1_j^H v1_{j+1}, and for the column a'
+//       after the window g' = Q^H a', c' = v1_{W-1}^H a'
+// The columns are decided in order exactly as in the one-column loop
+// (|v2_j|^2 = |v1_j|^2 - |h2_j|^2 against the same Q) up to and including the
+// first kept one, q = (v1_j - Q h2_j) / |v2_j|.  The column after it continues
+// in the one-column loop; its first-pass coefficients are g + h2 along Q and,
+// along q, (v1_j^H v1_{j+1} - h2_j^H h2_{j+1}) / |v2_j| (inside the window)
+// or (c' - h2_j^H g') / |v2_j| (a'), both from the sums above.  Columns after
+// that are redone.
+constexpr int LA_WMAX = 16;
+
+// One vector of the block's rows: 0 = kept column i, 1 = window vector i,
+// 2 = column i of A.
+__device__ __forceinline__ cplx la_vec(int kind, int i, int rr, const cplx* A, long long M, long long r0,
+                                       const cplx* qc, int nc, const cplx (*vw)[QB], const CoopSm& sm) {
+    if (kind == 0) return qcol(A, M, r0, qc, nc, i, rr, sm);
+    if (kind == 1) return vw[i][rr];
+    return A[r0 + rr + (long long)i * M];
+}
+
+// out[p] = sum over the block's rows of conj(L_p) R_p for p < P, where
+// pair(p, lk, li, rk, ri) names the two vectors; row slices of a power-of-two
+// width are reduced by shuffles (as in coop_partials).
+template <class PairF>
+__device__ void la_dots(int P, PairF pair, cplx* out, const cplx* A, long long M, long long r0, int nrows,
+                        const cplx* qc, int nc, const cplx (*vw)[QB], CoopSm& sm) {
+    const int t = threadIdx.x;
+    if (P > QB) {
+        for (int p = t; p < P; p += QB) {
+            int lk, li, rk, ri;
+            pair(p, lk, li, rk, ri);
+            cplx s0 = make_double2(0.0, 0.0);
+            for (int rr = 0; rr < nrows; ++rr) {
+                cplx a = la_vec(lk, li, rr, A, M, r0, qc, nc, vw, sm), b = la_vec(rk, ri, rr, A, M, r0, qc, nc, vw, sm);
+                s0.x = fma(a.x, b.x, fma(a.y, b.y, s0.x));
+                s0.y = fma(a.x, b.y, fma(-a.y, b.x, s0.y));
+            }
+            out[p] = s0;
+        }
+        __syncthreads();
+        return;
+    }
+    int sl = 1;
+    while (2 * sl * P <= QB) sl *= 2;
+    const int p = t / sl, q = t % sl;
+    cplx sv = make_double2(0.0, 0.0);
+    if (p < P) {
+        int lk, li, rk, ri;
+        pair(p, lk, li, rk, ri);
+        for (int rr = q; rr < nrows; rr += sl) {
+            cplx a = la_vec(lk, li, rr, A, M, r0, qc, nc, vw, sm), b = la_vec(rk, ri, rr, A, M, r0, qc, nc, vw, sm);
+            sv.x = fma(a.x, b.x, fma(a.y, b.y, sv.x));
+            sv.y = fma(a.x, b.y, fma(-a.y, b.x, sv.y));
+        }
+    }
+    const int seg = sl < 32 ? sl : 32;
+    for (int o = seg / 2; o > 0; o >>= 1) {
+        sv.x += __shfl_xor_sync(0xffffffffu, sv.x, o);
+        sv.y += __shfl_xor_sync(0xffffffffu, sv.y, o);
+    }
+    if (q % 32 == 0) sm.red[t / seg] = sv;
+    __syncthreads();
+    const int per = sl / seg;
+    if (t < P) {
+        cplx a = sm.red[t * per];
+        for (int w = 1; w < per; ++w) a = cadd(a, sm.red[t * per + w]);
+        out[t] = a;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D, cplx* R, int* flags, cplx* part,
                                                      cplx* red_out, unsigned* bar, int* err, int nc_max) {
-    extern __shared__ cplx qc[];   // nc_max cached columns of QCS rows
+    // dynamic shared memory: nc_max cached columns of QCS rows, then the
+    // look-ahead window (this block's rows of v1_j)
+    extern __shared__ cplx dyn[];
+    cplx* qc = dyn;
+    cplx(*vw)[QB] = reinterpret_cast<cplx(*)[QB]>(dyn + (long long)nc_max * QCS);
     __shared__ CoopSm sm;
+    __shared__ cplx la_g[PSTRIDE];     // look-ahead: g_j = Q^H a_j (column j at j * nq)
+    __shared__ double la_s2[LA_WMAX];
     const int G = gridDim.x, t = threadIdx.x;
     const long long r0 = (long long)blockIdx.x * QB;
     const int nrows = (int)min((long long)QB, M - r0);
@@ -540,14 +622,18 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
     sm.an[t] = (own && D > 1) ? A[r + M] : make_double2(0.0, 0.0);
     if (t == 0) sm.nnz = 0;
     __syncthreads();
+    int seq = 0;        // reductions so far: partial rows alternate between two buffers
+    int la_w = 4;       // look-ahead window width
     for (int k = 0; k < D; ++k) {
         const int n = sm.nnz, E = 2 * n + 2;
         const int nc = min(n, nc_max);
         // prefetch a_{k+2}; its latency hides behind the synchronisation
         const cplx pre = (own && k + 2 < D) ? A[r + (long long)(k + 2) * M] : make_double2(0.0, 0.0);
-        cplx* prow = part + ((long long)(k & 1) * G + blockIdx.x) * PSTRIDE;
-        coop_partials(A, M, r0, nrows, n, qc, nc, k == 0 ? fro : 0.0, G == 1 ? sm.hb : prow, sm);
-        if (!coop_reduce(part + (long long)(k & 1) * G * PSTRIDE, G, E, red_out, bar, err, sm)) return;
+        cplx* pbuf = part + (long long)(seq & 1) * G * PSTRIDE;
+        ++seq;
+        coop_partials(A, M, r0, nrows, n, qc, nc, k == 0 ? fro : 0.0, G == 1 ? sm.hb : pbuf + blockIdx.x * PSTRIDE,
+                      sm);
+        if (!coop_reduce(pbuf, G, E, red_out, bar, err, sm)) return;
         // decide column k; first-pass coefficient of a_{k+1} along q_k
         if (k == 0 && t == 0) sm.fro2 = sm.hb[1].y;
         __syncthreads();
@@ -600,6 +686,148 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
         }
         sm.an[t] = pre;
         __syncthreads();
+        if (!sm.dep) continue;
+        // column k was dependent: decide the following columns a window at a
+        // time while the kept set stays the same
+        int k0 = k + 1;
+        bool resume = false;   // the one-column loop continues at column k0
+        while (k0 < D && !resume) {
+            const int nq = sm.nnz, ncq = min(nq, nc_max);
+            const int cap = (PSTRIDE - nq - 1) / (nq + 2);   // widest window whose sums fit a partial row
+            if (k0 == k + 1 && cap < 2) break;    // kept set too wide: stay column by column (state in place)
+            const int W = min(min(min(la_w, LA_WMAX), D - k0), cap);   // >= 1
+            const bool after = k0 + W < D;
+            const int ka = k0 + W;                // the column after the window
+            // L1: g_j = Q^H a_j, kept in la_g; v1_j = a_j - Q g_j into vw
+            if (nq > 0) {
+                cplx* pb = part + (long long)(seq & 1) * G * PSTRIDE;
+                ++seq;
+                la_dots(nq * W, [&](int p, int& lk, int& li, int& rk, int& ri) {
+                            lk = 0; li = p % nq; rk = 2; ri = k0 + p / nq;
+                        }, G == 1 ? sm.hb : pb + blockIdx.x * PSTRIDE, A, M, r0, nrows, qc, ncq, vw, sm);
+                if (!coop_reduce(pb, G, nq * W, red_out, bar, err, sm)) return;
+                for (int e = t; e < nq * W; e += QB) la_g[e] = sm.hb[e];
+                __syncthreads();
+            }
+            for (int j = 0; j < W; ++j) {
+                cplx v = make_double2(0.0, 0.0);
+                if (own) {
+                    cplx a = A[r + (long long)(k0 + j) * M];
+                    cplx u = coop_combo(A, M, r0, t, qc, ncq, nq, la_g + j * nq, sm);
+                    v = make_double2(a.x - u.x, a.y - u.y);
+                }
+                vw[j][t] = v;
+            }
+            __syncthreads();
+            // L2: h2 (nq W, column j at j * nq), |v1_j|^2 (W), v1_j^H v1_{j+1}
+            // (W - 1), g' (nq), c' (1)
+            const int o_nv = nq * W, o_x = o_nv + W, o_g = o_x + (W - 1), o_c = o_g + nq, E2 = o_c + 1;
+            {
+                cplx* pb = part + (long long)(seq & 1) * G * PSTRIDE;
+                ++seq;
+                la_dots(E2, [&](int p, int& lk, int& li, int& rk, int& ri) {
+                            if (p < o_nv) { lk = 0; li = p % nq; rk = 1; ri = p / nq; }
+                            else if (p < o_x) { lk = 1; li = p - o_nv; rk = 1; ri = p - o_nv; }
+                            else if (p < o_g) { lk = 1; li = p - o_x; rk = 1; ri = p - o_x + 1; }
+                            else if (p < o_c) { lk = 0; li = p - o_g; rk = after ? 2 : 1; ri = after ? ka : 0; }
+                            else { lk = 1; li = W - 1; rk = after ? 2 : 1; ri = after ? ka : W - 1; }
+                        }, G == 1 ? sm.hb : pb + blockIdx.x * PSTRIDE, A, M, r0, nrows, qc, ncq, vw, sm);
+                if (!coop_reduce(pb, G, E2, red_out, bar, err, sm)) return;
+            }
+            for (int j = t; j < W; j += QB) {
+                double s2 = 0.0;
+                for (int i = 0; i < nq; ++i) {
+                    cplx h = sm.hb[j * nq + i];
+                    s2 += h.x * h.x + h.y * h.y;
+                }
+                la_s2[j] = s2;
+            }
+            __syncthreads();
+            // decisions in column order up to the first kept column
+            if (t == 0) {
+                const double f = sqrt(sm.fro2);
+                int js = -1;
+                double nrm = 0.0;
+                for (int j = 0; j < W; ++j) {
+                    nrm = sqrt(fmax(sm.hb[o_nv + j].x - la_s2[j], 0.0));
+                    const int dep = (f == 0.0) || (nrm <= QR_TOL * f);
+                    if (b0) {
+                        R[(long long)(k0 + j) * D + (k0 + j)] = make_double2(dep ? 0.0 : nrm, 0.0);
+                        flags[k0 + j] = dep;
+                    }
+                    if (!dep) {
+                        js = j;
+                        break;
+                    }
+                }
+                sm.dep = js;
+                sm.scale = js >= 0 ? 1.0 / nrm : 0.0;
+            }
+            __syncthreads();
+            const int js = sm.dep, nd = js >= 0 ? js + 1 : W;
+            if (b0)
+                for (int e = t; e < nq * nd; e += QB)
+                    R[(long long)(k0 + e / nq) * D + sm.nz[e % nq]] = cadd(la_g[e], sm.hb[e]);
+            // finalise the decided columns: zero if dependent, q if kept
+            if (own)
+                for (int j = 0; j < nd; ++j) {
+                    cplx w = make_double2(0.0, 0.0);
+                    if (j == js) {
+                        cplx v = vw[j][t], u = coop_combo(A, M, r0, t, qc, ncq, nq, sm.hb + j * nq, sm);
+                        w = make_double2((v.x - u.x) * sm.scale, (v.y - u.y) * sm.scale);
+                        if (nq < nc_max) qc[nq * QCS + t] = w;
+                    }
+                    A[r + (long long)(k0 + j) * M] = w;
+                }
+            __syncthreads();
+            if (js < 0) {   // the whole window was dependent
+                k0 += W;
+                la_w = min(2 * la_w, LA_WMAX);
+                continue;
+            }
+            la_w = max(4, la_w / 2);
+            const int kn = k0 + js + 1;           // next column, back in the one-column loop
+            if (kn >= D) {
+                k0 = D;
+                break;
+            }
+            // first-pass coefficients of column kn: [g + h2 (inside) or g' (after) ; along q]
+            const bool inside = js + 1 < W;
+            if (t == 0) {
+                cplx c = inside ? sm.hb[o_x + js] : sm.hb[o_c];
+                double px = 0.0, py = 0.0;    // h2_js^H (h2_{js+1} or g')
+                for (int i = 0; i < nq; ++i) {
+                    cplx h = sm.hb[js * nq + i];
+                    cplx o = inside ? sm.hb[(js + 1) * nq + i] : sm.hb[o_g + i];
+                    px += h.x * o.x + h.y * o.y;
+                    py += h.x * o.y - h.y * o.x;
+                }
+                sm.hk = make_double2(sm.scale * (c.x - px), sm.scale * (c.y - py));
+            }
+            for (int i = t; i < nq; i += QB)
+                sm.h1s[i] = inside ? cadd(la_g[(js + 1) * nq + i], sm.hb[(js + 1) * nq + i]) : sm.hb[o_g + i];
+            __syncthreads();
+            if (t == 0) {
+                sm.h1s[nq] = sm.hk;
+                sm.nz[nq] = k0 + js;
+                sm.nnz = nq + 1;
+            }
+            __syncthreads();
+            // v1 of column kn = a_kn - [Q q] h1s (its first pass), a_next = a_{kn+1}
+            const int n1 = nq + 1, nc1 = min(n1, nc_max);
+            if (own) {
+                cplx a = A[r + (long long)kn * M], u = coop_combo(A, M, r0, t, qc, nc1, n1, sm.h1s, sm);
+                sm.v1[t] = make_double2(a.x - u.x, a.y - u.y);
+                sm.an[t] = kn + 1 < D ? A[r + (long long)(kn + 1) * M] : make_double2(0.0, 0.0);
+            } else {
+                sm.an[t] = make_double2(0.0, 0.0);
+            }
+            __syncthreads();
+            k0 = kn;
+            resume = true;
+        }
+        if (k0 >= D) break;     // every column decided and finalised
+        k = k0 - 1;             // the loop's increment brings it to k0
     }
 }
 
@@ -930,11 +1158,11 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(cplx) * QC_MAX * QCS));
+                             (int)(sizeof(cplx) * (QC_MAX * QCS + LA_WMAX * QB)));
         for (int i = 0; i < 3; ++i) {
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, QB,
-                                                          sizeof(cplx) * nc_opts[i] * QCS);
+                                                          sizeof(cplx) * (nc_opts[i] * QCS + LA_WMAX * QB));
             coop_limit[i] = coop ? nsm * per_sm : 0;
         }
     }
@@ -942,7 +1170,7 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
     for (int i = 0; i < 3 && !coop_done && D <= MAXD; ++i) {
         if (G > coop_limit[i]) continue;
         int nc = nc_opts[i];
-        size_t smem = sizeof(cplx) * nc * QCS;
+        size_t smem = sizeof(cplx) * (nc * QCS + LA_WMAX * QB);
         // the barrier leaves its arrival count at zero after every completed
         // wait, so it needs a reset only after an error
         void* args[] = {(void*)&A, (void*)&MM, (void*)&D, (void*)&R, (void*)&ws.flags, (void*)&ws.part,
