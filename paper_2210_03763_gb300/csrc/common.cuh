@@ -66,6 +66,8 @@ int k_orth_update_ex(const cplx* V, long long ld, int nv, const cplx* partial_in
                      int mode, cplx* partial_dots, double* partial_norm, cplx* h_out, int accumulate,
                      long long skip_col, cudaStream_t s);
 int k_scale_copy_dev(const cplx* x, long long n, const double* scale, cplx* y, cudaStream_t s);
+// x <- x * sqrt(sum pr / sum px) with px, pr norm^2 partials (k_norm2_partial)
+int k_rescale_to_norm(cplx* x, long long n, const double* px, int Gx, const double* pr, int Gr, cudaStream_t s);
 int k_krylov_start_ex(KrylovScalars* ks, const double* nrm2_partial, long long n, cudaStream_t s);
 int k_krylov_scalars_ex(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial,
                         long long n, int j, double zr, double zi, double tol, cudaStream_t s);

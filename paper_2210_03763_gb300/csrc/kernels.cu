@@ -168,6 +168,25 @@ __global__ void scale_copy_kernel(const cplx* x, long long n, const double* scal
     }
 }
 
+// x <- x * sqrt(sum(pr) / sum(px)): rescale x to the norm given by the
+// partial sums pr (each block sums both partial lists in the same order).
+__global__ void rescale_to_norm_kernel(cplx* x, long long n, const double* px, int Gx, const double* pr, int Gr) {
+    __shared__ double f;
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int g = 0; g < Gx; ++g) a += px[g];
+        for (int g = 0; g < Gr; ++g) b += pr[g];
+        f = a > 0.0 ? sqrt(b / a) : 1.0;
+    }
+    __syncthreads();
+    const double ff = f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        cplx v = x[e];
+        x[e] = make_double2(v.x * ff, v.y * ff);
+    }
+}
+
 __global__ void combine_kernel(const cplx* V, long long ld, int nv, const KrylovScalars* ks, cplx* y,
                                long long n) {
     __shared__ cplx c[KRYLOV_MMAX];
@@ -387,6 +406,11 @@ int k_orth_update_ex(const cplx* V, long long ld, int nv, const cplx* partial_in
 
 int k_scale_copy_dev(const cplx* x, long long n, const double* scale, cplx* y, cudaStream_t s) {
     scale_copy_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scale, y);
+    return 1;
+}
+
+int k_rescale_to_norm(cplx* x, long long n, const double* px, int Gx, const double* pr, int Gr, cudaStream_t s) {
+    rescale_to_norm_kernel<<<grid_for(n), 256, 0, s>>>(x, n, px, Gx, pr, Gr);
     return 1;
 }
 

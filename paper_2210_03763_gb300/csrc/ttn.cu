@@ -137,6 +137,8 @@ struct ttn_ctx {
     cplx* kh2 = nullptr;
     cplx* kpart = nullptr;    // 2 * RED_BLOCKS * (KRYLOV_MMAX + 1)
     double* kpn = nullptr;    // RED_BLOCKS
+    double* apx = nullptr;    // RED_BLOCKS: norm^2 partials of an absorbed node
+    double* apr = nullptr;    // RED_BLOCKS: norm^2 partials of the absorbed link matrix
     int* hflag = nullptr;     // pinned host: converged, nonfinite
     QrScratch qr{};
     std::map<std::pair<int, int>, int*> cand;   // (node, leg) -> candidate rows
@@ -655,11 +657,28 @@ void qr_leg(ttn_ctx* c, int k, int o) {
                                   PERM[o][2], 1, c->stream);
 }
 
-// node k <- Rbuf x_leg node k   (absorb the link matrix; FP64, see gemm())
-void absorb(ttn_ctx* c, int k, int leg) {
-    ForceFp64 f64;
+// node k <- Rbuf x_leg node k   (absorb the link matrix).
+// Node k is an isometry from leg `leg` to its other two legs here (it was
+// just QR'd towards this link), so the new centre's norm equals |R|_F in
+// exact arithmetic.  In split precision the contraction's norm error is what
+// drifts the state's norm (a plain split absorb lost ~1e-5 per step); the
+// product is therefore rescaled to |R|_F with FP64 reductions, leaving only
+// its direction error (~5e-7 relative, a second-order infidelity).  In FP64
+// mode, and for gauge-only moves (`gauge_only`: observables must not perturb
+// the state they read), the absorb is a plain FP64 contraction.
+void absorb(ttn_ctx* c, int k, int leg, bool gauge_only = false) {
     const Node& nd = c->nodes[k];
-    leg_apply(c, c->Rbuf, nd.d[leg], c->T[k], nd.d, leg, c->tmp[1], 0.0);
+    const long long D = nd.d[leg];
+    if (c->prec == TTN_SPLIT_TF32X3 && !g_force_fp64 && !gauge_only) {
+        c->stats[3] += k_norm2_partial(c->Rbuf, D * D, c->apr, c->stream);
+        leg_apply(c, c->Rbuf, nd.d[leg], c->T[k], nd.d, leg, c->tmp[1], 0.0);
+        c->stats[3] += k_norm2_partial(c->tmp[1], nd.s, c->apx, c->stream);
+        c->stats[3] += k_rescale_to_norm(c->tmp[1], nd.s, c->apx, red_blocks_for(nd.s), c->apr,
+                                         red_blocks_for(D * D), c->stream);
+    } else {
+        ForceFp64 f64;
+        leg_apply(c, c->Rbuf, nd.d[leg], c->T[k], nd.d, leg, c->tmp[1], 0.0);
+    }
     std::swap(c->T[k], c->tmp[1]);
 }
 
@@ -744,7 +763,7 @@ void centre_to(ttn_ctx* c, int k) {
         int u = c->nodes[cur].child[0] == ch ? 0 : 1;
         qr_leg(c, cur, u);
         build_down(c, cur, u);
-        absorb(c, ch, 2);
+        absorb(c, ch, 2, true);
         cur = ch;
     }
     c->centre = k;
@@ -761,7 +780,7 @@ void centre_to_root(ttn_ctx* c) {
         int u = c->nodes[par].child[0] == cur ? 0 : 1;
         qr_leg(c, cur, 2);
         build_up(c, cur);
-        absorb(c, par, u);
+        absorb(c, par, u, true);
         cur = par;
     }
     c->centre = c->root;
@@ -963,6 +982,8 @@ void allocate(ttn_ctx* c) {
     c->kh2 = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1));
     c->kpart = (cplx*)dalloc(c, sizeof(cplx) * 2 * RED_BLOCKS * (MAX_CHI + 2));
     c->kpn = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
+    c->apx = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
+    c->apr = (double*)dalloc(c, sizeof(double) * RED_BLOCKS);
     long long mq = 1;   // largest QR row count: max over nodes and legs of s / d_leg
     for (int k = 0; k < nn; ++k)
         for (int u = 0; u < 3; ++u) mq = std::max(mq, c->nodes[k].s / c->nodes[k].d[u]);
