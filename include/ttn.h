@@ -224,8 +224,8 @@ ttn_status ttn_reset_stats(ttn_ctx* ctx);
  * It calls no cudaMalloc, cudaFree or allocating library routine.  The packed
  * operands live in one file-scope device array of 8 MiB, which every GPU that
  * loads this library holds until the process exits; a shape whose packed
- * operands need more (about 2 * (round_up(2 min(M,N), 128) + round_up(
- * max(M,N), 64)) * round_up(2K, 32) * 4 bytes) returns TTN_ERR_ARG and does
+ * operands need more (about 2 * (round_up(max(M,N), 128) + round_up(
+ * 2 min(M,N), 64)) * round_up(2K, 32) * 4 bytes) returns TTN_ERR_ARG and does
  * nothing.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress, with the device current); make that first call
  * before any stream capture.  Every call shares the one array and it keeps

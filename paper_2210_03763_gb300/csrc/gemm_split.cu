@@ -4,27 +4,30 @@
 // FP32 accumulation in tensor memory (the lo*lo term, ~2^-22 relative, is
 // dropped).  Result accuracy is close to FP32 (about 1e-7 relative).
 //
-// Complex numbers use a real embedding.  The side with fewer rows ("P", R x K)
-// becomes 2R x 2K real rows, the other side ("Q", N x K) N x 2K, with the K
+// Complex numbers use a real embedding.  One side ("P", R x K) becomes
+// R x 2K real rows, the other side ("Q", N x K) 2N x 2K, with the K
 // axis interleaved as k' = 2k + half:
-//   P row 2r   : ( Re p, -Im p )      Q row n : ( Re q, Im q )
-//   P row 2r+1 : ( Im p,  Re p )
-// so  C~(2r, n) = Re(sum_k p q) and C~(2r+1, n) = Im(sum_k p q).
+//   P row r : ( Re p, Im p )        Q row 2n   : ( Re q, -Im q )
+//                                   Q row 2n+1 : ( Im q,  Re q )
+// so  C~(r, 2n) = Re(sum_k p q) and C~(r, 2n+1) = Im(sum_k p q): the real and
+// imaginary parts of an output sit in adjacent TMEM columns of one lane.
+// The doubled side is chosen by packed bytes (plan_for).
 //
-// Two kernels per contraction:
+// Two kernels per contraction (three with split-K):
 //  1. pack_kernel: gathers the strided FP64 operand (any GemmArgs strides,
 //     optional conjugation, batches) into zero-padded K-major FP32 hi/lo
 //     planes; HBM bound, coalesced float2 stores.
 //  2. tcgen05 GEMM: persistent, one CTA per SM walking 128 x 64 tiles of C~,
-//     10 warps; the stage ring and TMEM buffers run on across tiles.  Warp 8 issues
-//     TMA loads (128-byte swizzle, no multicast) into a 4-stage ring, warp 9
-//     issues 12 tcgen05.mma per 32-wide K slice into one of four TMEM
-//     accumulators and releases stages with tcgen05.commit; warps 0-7 drain
-//     finished K chunks from TMEM (tcgen05.ld 32x32b, two warps per lane
-//     quadrant, 32 columns each) into float-float sums and finally write
-//     alpha * C~ + beta * C in FP64.
-//  Every mbarrier wait is bounded; on timeout the kernel sets an error flag,
-//  skips the rest, frees its TMEM and returns.
+//     18 warps; the stage ring and TMEM buffers run on across tiles.  Warp 16
+//     issues TMA loads (128-byte swizzle, no multicast) into a 4-stage ring,
+//     warp 17 issues 12 tcgen05.mma per 32-wide K slice into one of four TMEM
+//     accumulators and releases stages with tcgen05.commit; warps 0-15 drain
+//     finished K chunks from TMEM (tcgen05.ld 32x32b, four warps per lane
+//     quadrant, 16 columns each) into float-float sums and finally write
+//     alpha * C + beta * C in FP64, one complex entry per pair of columns.
+//  3. splitk_reduce_kernel when K is split into ranges (few output tiles).
+//  Every mbarrier wait is bounded by time; on timeout the kernel sets an
+//  error flag, lets its own copies and MMAs finish, frees its TMEM and returns.
 #include "common.cuh"
 
 #include <cuda.h>
@@ -215,7 +218,7 @@ struct PackArgs {
     long long s_r, s_ki, s_ko, s_bi, s_bo;   // strides of (row, k_in, k_out, batch_in, batch_out)
     int R, Ki, Ko, Bi, Bo;
     int conj;
-    int embed;         // 1: P side (2 rows per complex row), 0: Q side
+    int embed;         // 1: Q side (2 rows per complex row), 0: P side
     int Rp, Kp;        // padded output rows (real) and K' (fp32 elements)
     float* hi;
     float* lo;
@@ -484,22 +487,22 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             }
             if (!ok) break;
             const int trow = quad * 32 + lane;                  // row of C~ inside the tile
-            const int prow = pt * BM + trow;                    // P real row within the batch
-            const int pr = prow >> 1;                           // complex row of P
+            const int pr = pt * BM + trow;                      // complex row of P
             const int bi = b % ea.Bi, bo = b / ea.Bi;
             cplx* C = ea.C + bi * ea.c_bi + bo * ea.c_bo;
             // split-K: this K range's partial sum, dense column-major, plain store
             cplx* Wt = ea.nsplit > 1 ? ea.W + ((long long)ks * ea.batches + b) * ea.M * (long long)ea.N : nullptr;
+            // columns 2q and 2q + 1 of C~ hold the real and imaginary parts of
+            // one entry (the Q side carries the real embedding), so each
+            // thread owns whole complex outputs
 #pragma unroll
-            for (int j = 0; j < DCOLS; ++j) {
-                double val = f32_to_f64(hi[j]) + f32_to_f64(lo[j]);
-                double other = __shfl_xor_sync(0xffffffffu, val, 1);
-                if (lane & 1) continue;
-                int qn = qt * BN + col0 + j;                    // Q row = the other index
-                int m = ea.swapped ? qn : pr;
-                int n = ea.swapped ? pr : qn;
+            for (int j = 0; j < DCOLS; j += 2) {
+                const int qn = (qt * BN + col0 + j) >> 1;       // complex row of Q = the other index
+                const int m = ea.swapped ? qn : pr;
+                const int n = ea.swapped ? pr : qn;
                 if (m >= ea.M || n >= ea.N) continue;
-                double re = val, im = other;
+                const double re = f32_to_f64(hi[j]) + f32_to_f64(lo[j]);
+                const double im = f32_to_f64(hi[j + 1]) + f32_to_f64(lo[j + 1]);
                 if (Wt) {
                     Wt[m + (long long)n * ea.M] = make_double2(re, im);
                     continue;
@@ -633,16 +636,22 @@ Plan plan_for(const GemmArgs& g, int max_split) {
     long long K = (long long)g.Ki * g.Ko;
     if (g.M <= 0 || g.N <= 0 || K < 16) return pl;
     if (std::min(g.M, g.N) < 16 || std::max(g.M, g.N) < 64) return pl;
-    pl.swapped = g.M > g.N;
-    pl.Rp_rows = pl.swapped ? g.N : g.M;
-    pl.Rq_rows = pl.swapped ? g.M : g.N;
-    pl.Pp = (int)round_up(2LL * pl.Rp_rows, BM);
-    pl.Qp = (int)round_up(pl.Rq_rows, BN);
-    pl.Kp = (int)round_up(2 * K, BK);
+    // P: one real row per complex row; Q: the real embedding (two real rows
+    // per complex row).  The doubled side is the one whose packed bytes cost
+    // less -- rows times the batches it is packed for (1 if all batches share
+    // it) -- and on a tie the smaller side.
     pl.batches = (long long)g.Bi * g.Bo;
-    if (pl.batches > 65535 || pl.Qp / BN > 65535) return pl;
     const bool a_b = (g.a_bi == 0 || g.Bi == 1) && (g.a_bo == 0 || g.Bo == 1);
     const bool b_b = (g.b_bi == 0 || g.Bi == 1) && (g.b_bo == 0 || g.Bo == 1);
+    const long long ra = (long long)g.M * (a_b ? 1 : pl.batches), rb = (long long)g.N * (b_b ? 1 : pl.batches);
+    const long long cost_a_p = ra + 2 * rb, cost_b_p = rb + 2 * ra;   // P = A side / P = B side
+    pl.swapped = cost_b_p < cost_a_p || (cost_b_p == cost_a_p && g.N > g.M);
+    pl.Rp_rows = pl.swapped ? g.N : g.M;
+    pl.Rq_rows = pl.swapped ? g.M : g.N;
+    pl.Pp = (int)round_up(pl.Rp_rows, BM);
+    pl.Qp = (int)round_up(2LL * pl.Rq_rows, BN);
+    pl.Kp = (int)round_up(2 * K, BK);
+    if (pl.batches > 65535 || pl.Qp / BN > 65535) return pl;
     pl.p_bcast = pl.swapped ? b_b : a_b;
     pl.q_bcast = pl.swapped ? a_b : b_b;
     size_t pe = (size_t)(pl.p_bcast ? 1 : pl.batches) * pl.Pp * pl.Kp;
@@ -713,8 +722,8 @@ int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, s
     }
     PackArgs& P = pl.swapped ? pb : pa;
     PackArgs& Q = pl.swapped ? pa : pb;
-    P.embed = 1; P.Rp = pl.Pp; P.hi = Ph; P.lo = Pl;
-    Q.embed = 0; Q.Rp = pl.Qp; Q.hi = Qh; Q.lo = Ql;
+    P.embed = 0; P.Rp = pl.Pp; P.hi = Ph; P.lo = Pl;
+    Q.embed = 1; Q.Rp = pl.Qp; Q.hi = Qh; Q.lo = Ql;
     if (pl.p_bcast) { P.Bi = 1; P.Bo = 1; }
     if (pl.q_bcast) { Q.Bi = 1; Q.Bo = 1; }
     int launches = 0;
