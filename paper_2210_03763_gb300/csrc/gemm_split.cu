@@ -294,6 +294,7 @@ struct EpiArgs {
     cplx alpha, beta;
     int mode;             // 0: alpha = 1, beta = 0; 1: alpha = 1, beta = 1; 2: general
     int* err;
+    int q_fast;           // tile order inside a batch: Q tiles fastest (else P tiles fastest)
     int nsplit;           // K ranges per output tile (split-K); > 1: partial results go to W
     int cps;              // chunks per K range
     cplx* W;              // nsplit x batches x N x M partial results (column-major per batch)
@@ -343,9 +344,24 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nchunk = (ea.nkb + CHUNK_KB - 1) / CHUNK_KB;
     const long long ntiles = (long long)ea.nsplit * ea.batches * ea.n_qtiles * ea.n_ptiles;
-    // work item t: P tile fastest, then Q tile, batch, K range; its chunks [c0, c1)
+    // work item t: the tile grid of a batch (the smaller tile count fastest,
+    // so that work items running together share the other operand's tile in
+    // L2), then batch, then K range; its chunks [c0, c1)
+    const long long grid_tiles = (long long)ea.n_ptiles * ea.n_qtiles;
+    auto tile_of = [&](long long t, int& pt, int& qt, int& b, int& ks) {
+        const long long w = t % grid_tiles, rest = t / grid_tiles;
+        if (ea.q_fast) {
+            qt = (int)(w % ea.n_qtiles);
+            pt = (int)(w / ea.n_qtiles);
+        } else {
+            pt = (int)(w % ea.n_ptiles);
+            qt = (int)(w / ea.n_ptiles);
+        }
+        b = (int)(rest % ea.batches);
+        ks = (int)(rest / ea.batches);
+    };
     auto krange = [&](long long t, int& c0, int& c1) {
-        const int ks = (int)(t / ((long long)ea.batches * ea.n_qtiles * ea.n_ptiles));
+        const int ks = (int)(t / (grid_tiles * ea.batches));
         c0 = ks * ea.cps;
         c1 = min(nchunk, c0 + ea.cps);
     };
@@ -378,9 +394,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             unsigned it = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int pt = (int)(t % ea.n_ptiles);
-                const long long rest = t / ea.n_ptiles;
-                const int qt = (int)(rest % ea.n_qtiles), b = (int)((rest / ea.n_qtiles) % ea.batches);
+                int pt, qt, b, ks;
+                tile_of(t, pt, qt, b, ks);
                 const int prow0 = b * ea.Pp + pt * BM, qrow0 = b * ea.Qp + qt * BN;
                 int c0, c1;
                 krange(t, c0, c1);
@@ -456,10 +471,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         unsigned cg = 0;
         bool ok = true;
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int pt = (int)(t % ea.n_ptiles);
-            const long long rest = t / ea.n_ptiles;
-            const int qt = (int)(rest % ea.n_qtiles), b = (int)((rest / ea.n_qtiles) % ea.batches);
-            const int ks = (int)(rest / ea.n_qtiles / ea.batches);
+            int pt, qt, b, ks;
+            tile_of(t, pt, qt, b, ks);
             int c0, c1;
             krange(t, c0, c1);
             float hi[DCOLS], lo[DCOLS];
@@ -771,10 +784,12 @@ int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, si
     ea.nsplit = pl.nsplit;
     ea.cps = pl.cps;
     ea.W = pl.nsplit > 1 ? reinterpret_cast<cplx*>(reinterpret_cast<uint8_t*>(workspace) + pl.w_off) : nullptr;
-    // persistent: one CTA per SM walks the tiles, P tiles fastest so CTAs
-    // sharing a Q tile run together and hit it in L2
+    // persistent: one CTA per SM walks the tiles, the smaller tile count
+    // fastest so that CTAs sharing the other operand's tile run together and
+    // hit it in L2 (an operand larger than L2 is then read about once)
     ea.n_ptiles = pl.Pp / BM;
     ea.n_qtiles = pl.Qp / BN;
+    ea.q_fast = ea.n_qtiles < ea.n_ptiles;
     ea.batches = (int)pl.batches;
     long long ntiles = (long long)ea.n_ptiles * ea.n_qtiles * pl.batches * pl.nsplit;
     unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms());
