@@ -3,13 +3,15 @@
 // Every contraction of the TDVP update -- a matrix on one leg of a 3-leg node
 // tensor, the channel sums of the cross terms, the environment
 // renormalisations X^H (op x X) -- is one call of this kernel with suitable
-// strides.  Tile: 64 or 16 complex outputs per side (picked from M and N),
+// strides.  Tile: 16, 32 or 64 complex outputs per side (picked from M and N),
 // 256 threads, up to 4 x 4 complex accumulators per thread, K staged through
 // shared memory in slices of 8.
 // GB300's FP64 pipe (about 2 DFMA/clk/SM) is the bound, not memory: a simple
 // register-tiled loop is enough to saturate it, so loads use generic strides
 // (with bounds checks that zero-fill) rather than TMA.
 #include "common.cuh"
+
+#include <algorithm>
 
 namespace {
 
@@ -24,7 +26,7 @@ __device__ __forceinline__ cplx cmul_acc(cplx acc, cplx a, cplx b) {
     return acc;
 }
 
-// Tile BM x BN (each 16 or 64), chosen from the problem shape so that small
+// Tile BM x BN (each 16, 32 or 64), chosen from the problem shape so that small
 // outputs (3 x 3 physical legs, 9 x 9 projections) do not spend GB300's scarce
 // FP64 throughput on padding.
 template <int BM, int BN>
@@ -130,14 +132,30 @@ void launch_tile(const GemmArgs& g, cudaStream_t stream) {
     zgemm_f64_kernel<BM, BN><<<grid, THREADS, 0, stream>>>(g);
 }
 
+// Tile width for one dimension: the widest of 16, 32, 64 whose padded size is
+// within 5 % of the least padded one (81 -> 32: 96 rows instead of 128).
+int tile_for(int x) {
+    auto pad = [&](int b) { return (long long)((x + b - 1) / b) * b; };
+    const long long best = std::min(pad(16), std::min(pad(32), pad(64)));
+    for (int b : {64, 32})
+        if (pad(b) * 20 <= best * 21) return b;
+    return 16;
+}
+
+template <int BM>
+void launch_n(const GemmArgs& g, cudaStream_t stream, int bn) {
+    if (bn == 16) launch_tile<BM, 16>(g, stream);
+    else if (bn == 32) launch_tile<BM, 32>(g, stream);
+    else launch_tile<BM, 64>(g, stream);
+}
+
 }  // namespace
 
 int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream) {
     if (g.M <= 0 || g.N <= 0 || g.Bi <= 0 || g.Bo <= 0) return 0;
-    const bool sm = g.M <= 16, sn = g.N <= 16;
-    if (sm && sn) launch_tile<16, 16>(g, stream);
-    else if (sm) launch_tile<16, 64>(g, stream);
-    else if (sn) launch_tile<64, 16>(g, stream);
-    else launch_tile<64, 64>(g, stream);
+    const int bm = tile_for(g.M), bn = tile_for(g.N);
+    if (bm == 16) launch_n<16>(g, stream, bn);
+    else if (bm == 32) launch_n<32>(g, stream, bn);
+    else launch_n<64>(g, stream, bn);
     return 1;
 }
