@@ -10,16 +10,26 @@
 // earliest on ties), orthogonalised twice against Q and normalised.  R_kk is
 // real and >= 0; rows of R of dependent columns are zero.
 //
-// GB300's FP64 pipe (~7.8 GFLOP/s per SM) bounds this code, so every kernel
-// spreads the rows over all SMs (blocks of QB rows, one row per thread), and
-// projections skip columns that are still zero (dependent and not yet
-// filled): the work is O(M * D * rank) rather than O(M * D^2), which matters
-// for the low-entanglement states of GHZ circuits.  Per column three kernels:
+// GB300's FP64 pipe (~7.8 GFLOP/s per SM) bounds this code at full rank and
+// grid-synchronisation latency bounds it at low rank, so the rows are spread
+// over all SMs (blocks of QB rows) and projections skip columns that are
+// dependent: the work is O(M * D * rank) rather than O(M * D^2), which matters
+// for the low-entanglement states of GHZ circuits.
+//
+// Main path: the whole column loop is one cooperative kernel
+// (qr_coop_kernel) with one grid synchronisation per column (the second
+// pass of column k and the first pass of column k+1 share a reduction), and
+// a look-ahead that decides runs of dependent columns a window at a time.
+// Fallback when the row blocks cannot all be resident at once: three
+// kernels per column,
 //   K1 [decide column k-1 from its norm partials; dots of a_k with columns < k]
 //   K2 [sum the dot partials; a_k -= Q h; dots again]
-//   K3 [sum; a_k -= Q h2; norm partials]
+//   K3 [sum; a_k -= Q h2; norm partials].
 // Sums over blocks use the partials in one fixed order in every block (no
 // atomics), so all blocks see identical values and runs are reproducible.
+// Dependent columns are then filled by the closed form of the completion rule
+// (sc_select_kernel / sc_materialize_kernel) when the kept rank is <= 64,
+// else by the sequential kernels (rownorm, gs_unit, gs_second, normalize_col).
 #include "common.cuh"
 
 #include <algorithm>

@@ -245,12 +245,12 @@ double gemm_flops(const GemmArgs& g) {
     return 8.0 * g.M * (double)g.N * g.Ki * (double)g.Ko * g.Bi * (double)g.Bo;
 }
 
-// Contractions that write the state itself (absorbing a link matrix into a
-// node) and observables always run in FP64: the tensor core's FP32
-// accumulation rounds with a small bias (results shrink by ~1e-7 relative),
-// which in a state update is a norm loss that accumulates step after step,
-// while in an H_eff product or an environment it only perturbs the
-// generator (the Lanczos propagator stays unitary).
+// Observables and gauge-only moves always run in FP64 (ForceFp64): the
+// tensor core's FP32 accumulation rounds with a small bias (results shrink by
+// ~1e-7 relative), which in a contraction that writes the state is a norm
+// loss, while in an H_eff product or an environment it only perturbs the
+// generator (the Lanczos propagator stays unitary).  The sweep's own link
+// absorbs run in split precision with an exact FP64 norm restore (absorb).
 thread_local bool g_force_fp64 = false;
 struct ForceFp64 {
     bool old;
