@@ -15,7 +15,6 @@
 
 namespace {
 
-constexpr int BK = 8;
 constexpr int THREADS = 256;   // 16 x 16 threads; each owns a TM x TN register tile
 
 __device__ __forceinline__ cplx cmul_acc(cplx acc, cplx a, cplx b) {
@@ -32,6 +31,10 @@ __device__ __forceinline__ cplx cmul_acc(cplx acc, cplx a, cplx b) {
 template <int BM, int BN>
 __global__ void __launch_bounds__(THREADS) zgemm_f64_kernel(GemmArgs g) {
     constexpr int TM = BM / 16, TN = BN / 16;
+    // K slice per shared-memory stage: 8, or 32 for 16 x 16 tiles, whose small
+    // outputs (9 x 9 blocks) otherwise spend a global-memory round trip on
+    // every 8 of a long K (9 x 9 x 729: 92 round trips per launch)
+    constexpr int BK = (BM == 16 && BN == 16) ? 32 : 8;
     __shared__ cplx As[2][BK][BM];
     __shared__ cplx Bs[2][BK][BN];
 
