@@ -234,6 +234,22 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- our arm
+def replica_time(dist, secs, device):
+    """The slowest rank's timed seconds (max over ranks; `dist` is
+    torch.distributed after init_process_group, or None for one process)."""
+    if dist is None:
+        return secs
+    import torch
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, steps, t_max):
+    """Whole-job steps/s: every rank runs `steps` steps of its own replica."""
+    return world * steps / t_max
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,12 +300,8 @@ def main():
     clk.start()
     secs, stats, prof = time_steps(torch, g, stream, args.steps, profile=True)
     clocks = clk.stop()
-    t_max = secs
-    if dist:
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / t_max
+    t_max = replica_time(dist, secs, "cuda")
+    value = replica_value(world, args.steps, t_max)
 
     # e2e through the public API with host buffers: schedule in, populations out
     from paper_2210_03763_gb300 import workloads as W
