@@ -218,6 +218,29 @@ def to_pulse_array(schedule):
     return out
 
 
+def segmented_cz_schedule(pairs, n_seg, seed, omega=1.0, t0=0.0):
+    """CZ gates one after another, each as the Jaksch pulse sequence (pi on the
+    control, 2 pi on the target, pi on the control; gate time 2 pi / omega)
+    cut into n_seg equal piecewise-constant segments whose Rabi amplitudes are
+    drawn from N(omega, 0.1 omega) and detunings from N(0, 0.1 omega), seeded:
+    the inputs of gradient runs over pulse amplitudes.  n_seg must be a
+    multiple of 4 so that segments do not straddle the sub-pulses.  Returns
+    (rows, gate time); rows as in the module docstring."""
+    if n_seg % 4:
+        raise ValueError("n_seg must be a multiple of 4")
+    rng = np.random.default_rng(seed)
+    TG = 2 * math.pi / omega
+    rows = []
+    for g, (c, t) in enumerate(pairs):
+        base = t0 + g * TG
+        for k in range(n_seg):
+            s0, s1 = base + k * TG / n_seg, base + (k + 1) * TG / n_seg
+            atom = t if n_seg // 4 <= k < 3 * n_seg // 4 else c
+            rows.append([atom, s0, s1, 0.0, 0.0, rng.normal(omega, 0.1 * omega), 0.0,
+                         rng.normal(0.0, 0.1 * omega)])
+    return np.array(rows, dtype=np.float64), TG
+
+
 def random_constant_schedule(n_atoms, seed, t1=1e9, scale=1.0, atoms=None):
     """One constant segment per atom with seeded Gaussian amplitudes."""
     rng = np.random.default_rng(seed)
