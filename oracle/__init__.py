@@ -12,6 +12,8 @@ Plain, slow, complex128 NumPy/SciPy.  Two parts:
   Hamiltonian (Eq. 1 with the pair term of Eq. 2) for at most 9 atoms.
 * ``ttn``    -- Oracle-T, the single-site TTN-TDVP of Sec. "Tensor network
   simulations", step by step, in plain tensordot contractions.
+* ``adjoint`` -- the gradient of the final-state fidelity in piecewise-constant
+  pulse amplitudes, by exact reverse mode on the state vector (<= 6 atoms).
 
 Pins (values fixed by something other than this code) live in
 ``tests/test_oracle_*.py``.  Functions without a pin say "parity unpinned" in
