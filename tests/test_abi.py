@@ -63,3 +63,27 @@ def test_pulse_struct_matches_header():
     text = open(os.path.join(ROOT, "include", "ttn.h")).read()
     assert "Layout: 64 bytes" in text and PULSE_DTYPE.itemsize == 64
     assert PULSE_DTYPE.fields["t0"][1] == 8
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # the product path has no CPU fallback: without libttn.so the binding
+    # refuses to load
+    from paper_2210_03763_gb300 import native
+    monkeypatch.setattr(native, "_lib", None)
+    with pytest.raises(ImportError):
+        native.load(os.path.join(ROOT, "no_such_dir", "libttn.so"))
+
+
+def test_selftest_qr_rejects_bad_arguments_without_gpu(lib):
+    # size and candidate checks run before any CUDA call
+    D = ctypes.POINTER(ctypes.c_double)
+    a = (ctypes.c_double * 64)()
+    q = (ctypes.c_double * 64)()
+    r = (ctypes.c_double * 64)()
+    ap, qp, rp = (ctypes.cast(x, D) for x in (a, q, r))
+    assert lib.ttn_selftest_qr(ap, 3, 5, None, 0, qp, rp, None, None) == 1      # M < D
+    assert lib.ttn_selftest_qr(ap, 4, 0, None, 0, qp, rp, None, None) == 1      # D < 1
+    assert lib.ttn_selftest_qr(ap, 8, 300, None, 0, qp, rp, None, None) == 1    # D > 256
+    bad = (ctypes.c_int * 2)(0, 9)
+    assert lib.ttn_selftest_qr(ap, 8, 2, bad, 2, qp, rp, None, None) == 1       # row 9 of 8
+    assert lib.ttn_selftest_qr(None, 8, 2, None, 0, qp, rp, None, None) == 1    # no input
