@@ -150,81 +150,132 @@ def time_steps(torch, g, stream, k, profile=False):
 
 
 # ----------------------------------------------------------------- oracle leg
-def oracle_sample(n_samples=1):
+class OracleSampler:
     """Oracle (plain CPU complex128 TTN-TDVP) on the same workload, sampled.
 
-    One sample = one node visit at a level-4 node (the heaviest level of the
-    8x8 tree: (128,128,128) tensors): Krylov exponential of H_eff, QR towards
-    the parent, upward environment, backward link evolution.  A step visits
-    every non-root node twice; the per-step time is extrapolated from the
-    sample by the algorithmic flop model of a node visit (same Krylov count
-    assumed for every node).  Returns (steps/s, seconds per sample, note)."""
-    from oracle import ttn as ottn
-    xy, sched, amps = workload()
-    o = ottn.OracleTTN(LX, LY, CHI, xy, C6)
-    o.set_schedule(sched)
-    o.set_product_state(amps)
-    tr = o.tree
-    k = tr.level_nodes[-2][0]
-    # gauge moves root -> k (not timed)
-    path = []
-    x = k
-    while x != tr.root:
-        path.append(x)
-        x = tr.parent[x]
-    cur = tr.root
-    for ch in reversed(path):
-        u = 0 if tr.children[cur][0] == ("node", ch) else 1
-        o.T[cur], R = ottn.qr_leg(o.T[cur], u)
-        oth = [l for l in range(3) if l != u]
-        o.down[ch] = ottn.renormalize(o.T[cur], u, o.env(cur, oth[0]), o.env(cur, oth[1]), o.V)
-        o.T[ch] = ottn.apply_leg(R, o.T[ch], 2)
-        cur = ch
-    coef = o.coef(0.5 * DT)
-    times = []
-    for _ in range(n_samples):
+    Built once (with drive operators only for the atoms the CZ layer drives;
+    the others' coefficients are zero).  One sample = one node visit at a
+    level-4 node (the heaviest level of the 8x8 tree: (128,128,128) tensors):
+    Krylov exponential of H_eff, QR towards the parent, upward environment,
+    backward link evolution.  A step visits every non-root node twice; the
+    per-step time is extrapolated from the sample by the algorithmic flop
+    model of a node visit (same Krylov count assumed for every node)."""
+
+    def __init__(self):
+        from oracle import ttn as ottn
+        self.ottn = ottn
+        xy, sched, amps = workload()
+        drive = sorted({int(r[0]) for r in sched if r[3] != 0 or r[4] != 0 or r[5] != 0})
+        o = ottn.OracleTTN(LX, LY, CHI, xy, C6, drive_atoms=drive, amps=amps)
+        o.set_schedule(sched)
+        tr = o.tree
+        k = tr.level_nodes[-2][0]
+        # gauge moves root -> k (not timed)
+        path = []
+        x = k
+        while x != tr.root:
+            path.append(x)
+            x = tr.parent[x]
+        cur = tr.root
+        for ch in reversed(path):
+            u = 0 if tr.children[cur][0] == ("node", ch) else 1
+            o.T[cur], R = ottn.qr_leg(o.T[cur], u)
+            oth = [l for l in range(3) if l != u]
+            o.down[ch] = ottn.renormalize(o.T[cur], u, o.env(cur, oth[0]), o.env(cur, oth[1]), o.V)
+            o.T[ch] = ottn.apply_leg(R, o.T[ch], 2)
+            cur = ch
+        self.o, self.k = o, k
+        self.coef = o.coef(0.5 * DT)
+
+    def sample(self):
+        """Seconds of one node visit."""
+        o, k, ottn = self.o, self.k, self.ottn
         t0 = time.perf_counter()
-        o.node_evolve(k, 0.5 * DT, coef)
+        o.node_evolve(k, 0.5 * DT, self.coef)
         o.T[k], R = ottn.qr_leg(o.T[k], 2, o.allowed(k))
         o.up[k] = ottn.renormalize(o.T[k], 2, o.env(k, 0), o.env(k, 1), o.V)
-        R = o.link_evolve(R, o.up[k], o.down[k], 0.5 * DT, coef)
-        times.append(time.perf_counter() - t0)
+        R = o.link_evolve(R, o.up[k], o.down[k], 0.5 * DT, self.coef)
+        t = time.perf_counter() - t0
         o.T[k] = ottn.apply_leg(R, o.T[k], 2)
-    m = o.krylov_stats[-2][0] if len(o.krylov_stats) >= 2 else 8
+        return t
 
-    def visit_flops(kk):
-        d = tr.shape(kk)
-        s = d[0] * d[1] * d[2]
-        n = [len(tr.leg_sites(kk, u)) for u in range(3)]
-        r = [min(n[0], n[1]), min(n[0], n[2]), min(n[1], n[2])]
-        pair_d = [(d[0] + d[1]), (d[0] + d[2]), (d[1] + d[2])]
-        heff = 8 * s * (sum(d) + sum(ri * pd for ri, pd in zip(r, pair_d)))
-        qr = 16 * s * d[2]
-        env = 8 * s * (d[0] + d[2]) * (n[0] + n[1]) * 4
-        return m * heff + qr + env
-    per_sample = visit_flops(k)
-    per_step = sum(2 * visit_flops(kk) for kk in range(tr.n_nodes) if kk != tr.root) + visit_flops(tr.root)
-    t = min(times)
-    t_step = t * per_step / per_sample
+    def step_factor(self):
+        tr = self.o.tree
+        m = self.o.krylov_stats[-2][0] if len(self.o.krylov_stats) >= 2 else 8
+
+        def visit_flops(kk):
+            d = tr.shape(kk)
+            s = d[0] * d[1] * d[2]
+            n = [len(tr.leg_sites(kk, u)) for u in range(3)]
+            r = [min(n[0], n[1]), min(n[0], n[2]), min(n[1], n[2])]
+            pair_d = [(d[0] + d[1]), (d[0] + d[2]), (d[1] + d[2])]
+            heff = 8 * s * (sum(d) + sum(ri * pd for ri, pd in zip(r, pair_d)))
+            qr = 16 * s * d[2]
+            env = 8 * s * (d[0] + d[2]) * (n[0] + n[1]) * 4
+            return m * heff + qr + env
+        per_step = sum(2 * visit_flops(kk) for kk in range(tr.n_nodes) if kk != tr.root) + visit_flops(tr.root)
+        return per_step / visit_flops(self.k), m
+
+
+def oracle_sample(n_samples=1):
+    """(steps/s extrapolated, seconds per sample, note) of the 8x8 workload."""
+    smp = OracleSampler()
+    t = min(smp.sample() for _ in range(n_samples))
+    fac, m = smp.step_factor()
     note = ("oracle node visit at a (128,128,128) level-4 node (Krylov m=%d, QR, environment, link), "
-            "%.1f s; step time extrapolated by the flop model x%.1f" % (m, t, per_step / per_sample))
-    return 1.0 / t_step, t, note
+            "%.1f s; step time extrapolated by the flop model x%.1f" % (m, t, fac))
+    return 1.0 / (t * fac), t, note
+
+
+SMALL_STEP_CODE = """
+import json, sys, time
+sys.path.insert(0, %r)
+from oracle import ttn as ottn
+from paper_2210_03763_gb300 import workloads as W
+xy = W.square_lattice(4, 4)
+sched, TL = W.cz_layer_workload(4, 4, 2.0 ** 1.5)
+o = ottn.OracleTTN(4, 4, 64, xy, %r, amps=W.plus_state_amps(16))
+o.set_schedule(sched)
+o.step(%r)
+t0 = time.perf_counter()
+o.step(%r)
+print(json.dumps({"s_per_step": time.perf_counter() - t0}))
+"""
+
+
+def oracle_small_step(threads):
+    """Seconds of one real oracle step of the 4x4, chi = 64 CZ-layer workload
+    (r_G = sqrt(8) a, |+>^16), in a fresh process whose BLAS uses `threads`
+    threads (None: all cores).  A fresh interpreter, not a fork of this one."""
+    env = dict(os.environ)
+    if threads:
+        for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(threads)
+    code = SMALL_STEP_CODE % (ROOT, C6, DT, DT)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        return json.loads(r.stdout.strip().splitlines()[-1])["s_per_step"]
+    except Exception:
+        return None
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import multiprocessing
-    samples = []
-    note = ""
-    for _ in range(max(1, args.steps)):
-        v, t, note = oracle_sample(1)
-        samples.append(v)
-    value = statistics.median(samples)
+    smp = OracleSampler()
+    fac, _ = smp.step_factor()
+    for _ in range(args.warmup > 0 and 1 or 0):
+        smp.sample()
+    samples = [smp.sample() for _ in range(max(1, args.steps))]
+    fac, m = smp.step_factor()
+    t = statistics.median(samples)
+    value = 1.0 / (t * fac)
     cores = os.cpu_count()
+    note = ("each step: one oracle node visit at a (128,128,128) level-4 node (Krylov m=%d, QR, environment, "
+            "link), median %.1f s; step time extrapolated by the flop model x%.1f" % (m, t, fac))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": 0, "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "lattice": "8x8", "chi": CHI},
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
                              "sample": note},
@@ -258,6 +309,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed FP64 steps (0: skip the FP64 leg)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--profile-steps", type=int, default=2, help="steps of the instrumented second pass")
+    ap.add_argument("--full-rank-steps", type=int, default=2, help="timed steps from a full-rank start (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-out", default=None, help="write the kernel profile JSON here")
     ap.add_argument("--lattice", default=None, help="LXxLY of a smaller case (profiling); default 8x8")
@@ -296,12 +349,17 @@ def main():
     free1, _ = torch.cuda.mem_get_info()   # after warm-up: workspaces have grown to size
     if dist:
         dist.barrier()
+    # headline: K steps, no per-launch instrumentation
     clk = ClockSampler(local)
     clk.start()
-    secs, stats, prof = time_steps(torch, g, stream, args.steps, profile=True)
+    secs, stats, _ = time_steps(torch, g, stream, args.steps, profile=False)
     clocks = clk.stop()
     t_max = replica_time(dist, secs, "cuda")
     value = replica_value(world, args.steps, t_max)
+    # second pass: the same steps with CUDA events around every contraction and
+    # QR launch (kernel-class times for the roofline); not the headline
+    n_prof = max(1, min(args.steps, args.profile_steps))
+    p_secs, _, prof = time_steps(torch, g, stream, n_prof, profile=True)
 
     # e2e through the public API with host buffers: schedule in, populations out
     from paper_2210_03763_gb300 import workloads as W
@@ -322,19 +380,30 @@ def main():
 
     pk, peak_kind = peaks()
     tc = prof["tc_gemm"]
-    tf32_peak = pk["bf16_tflops"] * 1.1 / 2.25          # nominal TF32 : BF16 ratio
+    # a kernel timed inside seconds-long steps: the sustained BF16 rate, scaled
+    # by the nominal TF32 : BF16 ratio
+    tf32_peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * 1.1 / 2.25
     dominant = max(prof.items(), key=lambda kv: kv[1]["ms"])
     roof = None
     if tc["launches"] > 0 and tc["ms"] > 0:
         ach = tc["flops"] / (tc["ms"] * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": "tc_gemm_kernel (tcgen05 kind::tf32, 3xTF32)",
                 "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
-                "peak_source": "%s bf16 burst x 1.1/2.25 (nominal TF32:BF16)" % peak_kind,
-                "traffic": tc_traffic(), "launches": tc["launches"],
+                "peak_source": "%s bf16_tflops_sustained x 1.1/2.25 (nominal TF32:BF16), of %s" % (
+                    peak_kind, peak_kind),
+                "traffic": tc_traffic(), "launches": tc["launches"] / n_prof,
                 "traffic_source": "ncu dram__bytes_read+write per launch, mean over the first 150 tc_gemm "
                                   "launches of one 8x8 chi=128 step (profiles/tc_gemm_8x8_chi128_slice.md)",
-                "share_of_step": tc["ms"] / (secs * 1e3),
+                "share_of_step": tc["ms"] / (p_secs * 1e3),
                 "flops_counted": "algorithmic 8*M*N*K per complex contraction; tensor pipe executes 3x"}
+    pack = prof["split_pack"]
+    pack_line = None
+    if pack["launches"] > 0 and pack["ms"] > 0:
+        gbs = pack["bytes"] / (pack["ms"] * 1e-3) / 1e9
+        pack_line = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / pk["hbm_gbs"], "ms_per_step": pack["ms"] / n_prof,
+                     "bytes_per_step": pack["bytes"] / n_prof,
+                     "bytes_counted": "16 B read per complex operand element + hi/lo FP32 planes written"}
 
     result = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -344,10 +413,29 @@ def main():
                          "parallelism": "replicas" if world > 1 else "single",
                          "l2": "working set (node tensors, environments, Krylov basis) > 129 MB L2",
                          "device_mem_gb": round((free0 - free1) / 1e9, 2)},
-              "gpu_launches": int(stats["launches"]), "clocks": clocks, "e2e": e2e, "roofline": roof,
-              "profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()},
+              "gpu_launches": int(stats["launches"]), "launches_per_step": stats["launches"] / args.steps,
+              "clocks": clocks, "e2e": e2e, "roofline": roof, "split_pack": pack_line,
+              "profile": {k: {"launches": v["launches"] / n_prof, "ms_per_step": round(v["ms"] / n_prof, 3)}
+                          for k, v in prof.items()},
+              "profile_pass": {"steps": n_prof, "ms_per_step_instrumented": 1e3 * p_secs / n_prof},
               "dominant_kernel_class": dominant[0],
               "krylov_matvecs_per_step": stats["matvecs"] / max(1, args.steps)}
+
+    if args.full_rank_steps > 0 and rank == 0:
+        # the same workload from a random full-rank isometric TTN: every QR is
+        # full rank (the |+>^64 start keeps most bonds rank-deficient early on)
+        from oracle.tree import Tree   # tree shapes only (integer bookkeeping)
+        tr = Tree(LX, LY, CHI)
+        Ts = W.random_ttn_tensors([tr.shape(k) for k in range(tr.n_nodes)], 77)
+        h = make_ctx(native, native.SPLIT_TF32X3, stream)
+        for k, X in enumerate(Ts):
+            h.set_node(k, X)
+        h.refresh_envs()
+        h.step(DT)
+        fr_secs, _, _ = time_steps(torch, h, stream, args.full_rank_steps, profile=False)
+        result["full_rank_start"] = {"value": args.full_rank_steps / fr_secs, "unit": "steps/s",
+                                     "steps": args.full_rank_steps}
+        h.close()
 
     if args.fp64_steps > 0 and rank == 0:
         f = make_ctx(native, native.FP64, stream)
@@ -360,10 +448,14 @@ def main():
         ov = s2.overlap(f)
         infid = 1.0 - abs(ov) ** 2 / (s2.norm() * f.norm())
         fa = f_prof["f64_gemm"]
+        dfma = native.fp64_peak(0)
+        dmma = native.fp64_peak(1)
         result["fp64"] = {"value": args.fp64_steps / f_secs, "unit": "steps/s",
                           "speedup_split_over_fp64": value / (args.fp64_steps / f_secs),
                           "f64_gemm_tflops": fa["flops"] / max(1e-9, fa["ms"] * 1e-3) / 1e12,
-                          "f64_peak_tflops": 152 * 2.070e9 * 4 / 1e12}
+                          "f64_peak_tflops": max(dfma, dmma),
+                          "f64_peak_source": "measured in this run: DFMA chains %.3f, DMMA m8n8k4 %.3f TFLOP/s"
+                                             % (dfma, dmma)}
         result["fidelity_err"] = {"steps": 1 + args.fp64_steps,
                                   "infidelity_split_vs_fp64": infid,
                                   "abs_dE": abs(s2.energy() - f.energy()),
@@ -373,11 +465,19 @@ def main():
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         v, t, note = oracle_sample(1)
-        result["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-                                  "sample": note}
+        cores = os.cpu_count()
+        small_all = oracle_small_step(None)
+        small_one = oracle_small_step(1)
+        result["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                                  "sample": note,
+                                  "oracle_step_4x4_chi64": {
+                                      "workload": "4x4, chi=64, CZ layer of the r_G=sqrt(8)a schedule, |+>^16, "
+                                                  "one full oracle step, timed",
+                                      "s_per_step_all_cores": small_all, "cores": cores,
+                                      "s_per_step_1_core": small_one}}
     if args.profile_out and rank == 0:
         with open(args.profile_out, "w") as fo:
-            json.dump({"prof": prof, "stats": stats,
+            json.dump({"prof": prof, "profile_steps": n_prof, "stats": stats,
                        "records": {"columns": ["kind", "M", "N", "K", "batches", "ms", "flops"],
                                    "kinds": ["tc_gemm", "split_pack", "f64_gemm", "qr"],
                                    "rows": g.profile_records().tolist()}}, fo)

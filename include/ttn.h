@@ -208,6 +208,43 @@ ttn_status ttn_selftest_qr(const double* A, int M, int D, const int* cand, int n
 ttn_status ttn_profile_records(const ttn_ctx* ctx, double* out, int max_records, int* n_records);
 ttn_status ttn_reset_stats(ttn_ctx* ctx);
 
+/* Self-test of the contraction kernels on host data, no context needed:
+ * C = A B with A (M x K), B (K x N) and C (M x N) complex, column-major,
+ * interleaved (re, im) doubles in caller-owned host memory.  precision
+ * TTN_FP64 runs the FP64 kernel; TTN_SPLIT_TF32X3 runs the split-precision
+ * tensor-core path when the shape fills its tiles (else the FP64 kernel).
+ * *path (may be NULL) receives 1 when the tensor-core path ran, else 0; *ms
+ * (may be NULL) the device time of the contraction.  Sizes above 2^26
+ * elements per matrix -> TTN_ERR_ARG; a tensor-core wait that gave up ->
+ * TTN_ERR_TIMEOUT. */
+ttn_status ttn_selftest_contract_host(const double* A, const double* B, double* C, int M, int N, int K,
+                                      int precision, int* path, float* ms);
+
+/* FP64 throughput probe, no context needed: method 0 runs independent FP64
+ * fused multiply-add chains on every SM (the FP64 ALU, DFMA), method 1 chains
+ * of FP64 tensor-core instructions (mma.sync m8n8k4 f64, DMMA); *tflops
+ * receives the measured rate (2 flops per FMA).  The roofline of every FP64
+ * step (QR, Lanczos re-orthogonalisation, FP64 contractions) is set by this
+ * rate on GB300, not by HBM. */
+ttn_status ttn_selftest_fp64_peak(int method, double* tflops);
+
+/* Test hooks: host-side fault injection for the failure-detection tests (no
+ * GPU is faulted; every injected failure goes through a bounded path):
+ *   TTN_INJECT_TC_STALL    the next `value` tensor-core contractions make
+ *                          their drain warps wait on a barrier that nothing
+ *                          arrives at; the wait gives up after 1 ms and the
+ *                          launch aborts as on a real timeout (the caller sees
+ *                          TTN_ERR_TIMEOUT);
+ *   TTN_INJECT_KRYLOV_MMAX Krylov dimension capped at `value` (1..30; 0
+ *                          restores 30): a step that needs more returns
+ *                          TTN_ERR_KRYLOV;
+ *   TTN_INJECT_ALLOC_FAIL  the next `value` device allocations fail
+ *                          (TTN_ERR_ALLOC);
+ *   TTN_INJECT_NONE        clears every hook.
+ * Hooks are process-wide.  Bad kind or value -> TTN_ERR_ARG. */
+enum { TTN_INJECT_NONE = 0, TTN_INJECT_TC_STALL = 1, TTN_INJECT_KRYLOV_MMAX = 2, TTN_INJECT_ALLOC_FAIL = 3 };
+ttn_status ttn_test_inject(int kind, long long value);
+
 /* ---- allocation-free contraction ----------------------------------------
  * The paper has no counterpart to this call: it serves callers that cannot
  * allocate device memory at the point of the call (a host program whose
@@ -218,8 +255,10 @@ ttn_status ttn_reset_stats(ttn_ctx* ctx);
  * (re, im) doubles: A is M x K (lda = M), B is K x N (ldb = K), C is M x N
  * (ldc = M), caller-allocated; C is overwritten.  It runs the split-precision
  * tensor-core contraction (3xTF32, ~5e-7 of max|C|) when the shape fills the
- * tensor-core tiles, else the FP64 kernel, on `stream` (a cudaStream_t, NULL
- * for the legacy default stream), and returns without synchronising.
+ * tensor-core tiles, else the FP64 kernel (also when the driver offers no
+ * tensor-map encoder), on `stream` (a cudaStream_t, NULL for the legacy
+ * default stream), and returns once the contraction has finished: it
+ * synchronises `stream`, so that it can report the outcome.
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine.  The packed
  * operands live in one file-scope device array of 8 MiB, which every GPU that
@@ -232,7 +271,10 @@ ttn_status ttn_reset_stats(ttn_ctx* ctx);
  * the last call's contents: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Errors: TTN_ERR_ARG for null pointers, non-positive or too large sizes;
- * TTN_ERR_CUDA if a launch fails. */
+ * TTN_ERR_CUDA if a launch or the synchronisation fails; TTN_ERR_TIMEOUT if a
+ * bounded wait of the tensor-core pipeline gave up (C is then undefined; the
+ * error word in the scratch array is cleared, so the next call starts
+ * clean). */
 ttn_status ttn_contract_split_noalloc(const double* A, const double* B, double* C, int M, int N, int K,
                                       void* stream);
 

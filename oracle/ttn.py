@@ -45,11 +45,14 @@ class Env:
         self.ops = {}
 
 
-def physical_env(atom):
+def physical_env(atom, drive=True):
+    """Leaf environment of one atom: n always; sx, sz, |r><1| unless
+    ``drive`` is False (an atom that is never driven needs no drive operators;
+    the sums they enter then have zero coefficients)."""
     e = Env(3)
     if atom >= 0:
         e.sites = [atom]
-        for kind in KINDS:
+        for kind in KINDS if drive else ("n",):
             e.ops[(kind, atom)] = BARE[kind].copy()
     return e
 
@@ -70,6 +73,10 @@ def block_hamiltonian(env, coef):
     ox, oz, w, de = coef
     H = env.H.copy()
     for i in env.sites:
+        if ("rp", i) not in env.ops:       # drive operators not kept: atom never driven
+            assert ox[i] == 0 and oz[i] == 0 and w[i] == 0, "drive on atom %d without its operators" % i
+            H -= de[i] * env.ops[("n", i)]
+            continue
         rp = env.ops[("rp", i)]
         H += (ox[i] * env.ops[("sx", i)] + oz[i] * env.ops[("sz", i)]
               + w[i] * rp + np.conj(w[i]) * rp.conj().T
@@ -122,7 +129,13 @@ def qr_leg(X, leg, allowed=(None, None)):
 
 
 class OracleTTN:
-    def __init__(self, Lx, Ly, chi, xy=None, C6=0.0, r_cut=0.0):
+    def __init__(self, Lx, Ly, chi, xy=None, C6=0.0, r_cut=0.0, drive_atoms=None, amps=None):
+        """``drive_atoms``: atoms whose drive operators (sx, sz, |r><1|) are
+        carried through the environments; None keeps them for every atom.
+        Restricting them only skips operators whose coefficients are zero (a
+        drive on another atom is an error); measure(0) and measure(1) need
+        every atom's sz.  ``amps``: the initial product state (N x 3), all
+        atoms in |0> when None."""
         self.tree = Tree(Lx, Ly, chi)
         self.N = Lx * Ly
         if xy is None:
@@ -130,12 +143,13 @@ class OracleTTN:
         self.V = model.pair_couplings(xy, C6, r_cut)
         self.schedule = None
         self.t = 0.0
-        self.phys = [physical_env(a) for a in self.tree.leaf_atom]
+        keep = None if drive_atoms is None else set(int(a) for a in drive_atoms)
+        self.phys = [physical_env(a, keep is None or a in keep) for a in self.tree.leaf_atom]
         self.T = [None] * self.tree.n_nodes
         self.up = [None] * self.tree.n_nodes
         self.down = [None] * self.tree.n_nodes
         self.krylov_stats = []
-        self.set_product_state(np.tile([1.0, 0.0, 0.0], (self.N, 1)))
+        self.set_product_state(np.tile([1.0, 0.0, 0.0], (self.N, 1)) if amps is None else amps)
 
     # ---------------------------------------------------------------- setup
     def set_hamiltonian(self, xy, C6, r_cut=0.0):

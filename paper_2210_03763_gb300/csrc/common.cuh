@@ -22,6 +22,67 @@ struct GemmArgs {
 
 // Launch on `stream`; returns the number of kernels launched (0 if empty).
 int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream);
+
+// ---- split-precision building blocks (gemm_split.cu) -------------------------
+// Packing of one side of a split contraction into TF32 hi/lo planes: complex
+// element (row r, k, batch bi, bo) of src (strides s_r, s_ki (k % Ki),
+// s_ko (k / Ki), s_bi, s_bo) goes to real row (embed ? 2r : r) + bi*rb_i +
+// bo*rb_o, floats k_off + 2k of a row `pitch` floats long; embed = 1 is the
+// real embedding of the Q side (rows (Re, -Im) and (Im, Re)).  Rows
+// r in [R, Rpad) and k in [Ki*Ko, Kc) are written as zeros.
+struct SplitPackArgs {
+    const cplx* src;
+    long long s_r, s_ki, s_ko, s_bi, s_bo;
+    int R, Ki, Ko, Bi, Bo;
+    int conj, embed;
+    int Rpad, Kc;
+    long long rb_i, rb_o;
+    long long pitch, k_off;
+    float* hi;
+    float* lo;
+};
+int split_pack(const SplitPackArgs& p, cudaStream_t stream);
+
+// Packed output of a split contraction: the epilogue writes TF32 hi/lo
+// planes (as split_pack with embed = 0) at float2 position
+// (p % pd)*sp1 + (p / pd)*sp2 + (q % qd)*sq1 + (q / qd)*sq2 + bi*sbi + bo*sbo
+// for output (P row p, Q row q, batch bi, bo); hi/lo already offset to the
+// first slot.
+struct SplitOut {
+    float* hi;
+    float* lo;
+    int pd, qd;
+    long long sp1, sp2, sq1, sq2, sbi, sbo;
+};
+
+// One split contraction on packed planes: C(p, q) = alpha sum_k P(p, k) Q(q, k)
+// + beta C(p, q) per batch (bi, bo), P rows in tiles of 128, Q the embedded
+// side (2 real rows per complex row, tiles of 64).  Kp: K' in floats (a
+// multiple of 32), the same for both sides.
+struct SplitMma {
+    const float* Ph;
+    const float* Pl;
+    long long P_rows, P_pitch;   // rows in the planes, floats per row
+    const float* Qh;
+    const float* Ql;
+    long long Q_rows, Q_pitch;
+    int Kp;
+    int Pn, Qn;                  // valid complex rows of P and Q per batch
+    int Pp, Qp;                  // padded real rows of the tile grid per batch
+    int Bi, Bo;
+    long long p_sbi, p_sbo, q_sbi, q_sbo;   // real-row offsets of batch (bi, bo)
+    cplx* C;
+    long long c_p, c_q, c_bi, c_bo;
+    cplx alpha, beta;
+    const SplitOut* out;         // non-null: packed output (alpha = 1, beta = 0)
+    int max_split;               // split-K cap (1: none; forced to 1 with `out`)
+};
+constexpr int SPLIT_BM = 128, SPLIT_BN = 64, SPLIT_BK = 32;
+// bytes of split-K partial sums the contraction needs (0: no split-K)
+size_t split_mma_partials(const SplitMma& m);
+// Returns kernels launched, -1 on a bad shape or tensor map, -2 on missing
+// workspace.  err_flag: the int a timed-out wait sets.
+int split_mma(const SplitMma& m, int* err_flag, void* partials, size_t partial_bytes, cudaStream_t stream);
 // Split-precision tensor-core path (3xTF32 on tcgen05).  Returns kernels
 // launched, -1 when the shape is not handled there (too small: the caller
 // uses FP64), -2 when the workspace is smaller than split_workspace_bytes.
@@ -83,6 +144,10 @@ int k_assemble_block(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsite
                      const int* site_ids, const cplx* dops, int ndriven,
                      const int* driven_ids, const double* coef, cudaStream_t s);
 int k_check_finite(const cplx* x, long long n, int* flag, cudaStream_t s);
+double k_fp64_probe(int method, int blocks, int iters, double* out, cudaStream_t s);
+// G_i = sum_j W[j + nb*i] N_j, i < r (N: nb matrices of n entries, contiguous;
+// W real)
+int k_weighted_sum(const cplx* N, int nb, long long n, const double* W, int r, cplx* G, cudaStream_t s);
 
 // ---- QR (qr.cu) ----------------------------------------------------------------
 // QR kernels use one block per QR_ROWS rows; partial sums are sized
@@ -117,5 +182,13 @@ constexpr int QR_SC_MAXR = 64;   // structured completion when the kept rank r <
 // of the cooperative column loop gave up (A and R are then undefined).
 int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand,
             QrScratch& ws, cudaStream_t s, int* n_dependent_host);
+
+// ---- test hooks (ttn_test_inject in ttn.cu) -----------------------------------
+// Stall time in ns for the next tensor-core launch (0: none; consumes one
+// pending stall), the Krylov dimension cap (KRYLOV_MMAX unless lowered) and
+// whether the next device allocation is to fail (consumes one).
+unsigned long long test_take_tc_stall();
+int test_krylov_mmax();
+bool test_take_alloc_fail();
 
 #define TTN_LAUNCH_CHECK() (cudaGetLastError())

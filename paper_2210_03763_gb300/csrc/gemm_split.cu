@@ -38,7 +38,7 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 32;    // BK in fp32 elements = 128 bytes
+constexpr int BM = SPLIT_BM, BN = SPLIT_BN, BK = SPLIT_BK;   // BK in fp32 elements = 128 bytes
 constexpr int STAGES = 4;
 constexpr int A_TILE = BM * BK * 4;          // 16 KB per plane tile of P
 constexpr int B_TILE = BN * BK * 4;          // 8 KB per plane tile of Q
@@ -82,14 +82,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // role of this launch, or an earlier launch, has set the flag: one stuck
 // stage ends the whole launch within about WAIT_NS instead of every waiter
 // timing out in turn.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          unsigned long long limit_ns = WAIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (long long i = 1; i < SPIN_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63) == 0) {
             if (*(volatile int*)err) return false;
-            if (global_ns() - t0 > WAIT_NS) break;
+            if (global_ns() - t0 > limit_ns) break;
         }
     }
     atomicExch(err, 1);
@@ -213,33 +214,24 @@ __device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
 }
 
 // ----------------------------------------------------------------- packing
-struct PackArgs {
-    const cplx* src;
-    long long s_r, s_ki, s_ko, s_bi, s_bo;   // strides of (row, k_in, k_out, batch_in, batch_out)
-    int R, Ki, Ko, Bi, Bo;
-    int conj;
-    int embed;         // 1: Q side (2 rows per complex row), 0: P side
-    int Rp, Kp;        // padded output rows (real) and K' (fp32 elements)
-    float* hi;
-    float* lo;
-};
-
-__global__ void pack_kernel(PackArgs p) {
+// One thread per complex element (batch, row r < Rpad, k < Kc); entries with
+// r >= R or k >= Ki*Ko are written as zeros (tile padding).  Real row of
+// (r, bi, bo): (embed ? 2r : r) + bi*rb_i + bo*rb_o; float offset of k:
+// k_off + 2k in a row of `pitch` floats.
+__global__ void pack_kernel(SplitPackArgs p) {
     const int K = p.Ki * p.Ko;
-    const int half_k = p.Kp / 2;                       // complex k positions incl. padding
-    const int rows_src = p.embed ? p.Rp / 2 : p.Rp;    // complex rows incl. padding
-    const long long per_b = (long long)rows_src * half_k;
+    const long long per_b = (long long)p.Rpad * p.Kc;
     const long long total = per_b * p.Bi * p.Bo;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        long long b = e / per_b;
-        long long rem = e - b * per_b;
-        int r = (int)(rem / half_k);
-        int k = (int)(rem - (long long)r * half_k);
+        const long long b = e / per_b;
+        const long long rem = e - b * per_b;
+        const int r = (int)(rem / p.Kc);
+        const int k = (int)(rem - (long long)r * p.Kc);
+        const int bi = (int)(b % p.Bi), bo = (int)(b / p.Bi);
         double re = 0.0, im = 0.0;
         if (r < p.R && k < K) {
-            int bi = (int)(b % p.Bi), bo = (int)(b / p.Bi);
-            int ki = k % p.Ki, ko = k / p.Ki;
+            const int ki = k % p.Ki, ko = k / p.Ki;
             cplx v = p.src[bi * p.s_bi + bo * p.s_bo + r * p.s_r + ki * p.s_ki + ko * p.s_ko];
             re = v.x;
             im = p.conj ? __longlong_as_double(__double_as_longlong(v.y) ^ (long long)0x8000000000000000ULL) : v.y;
@@ -247,16 +239,15 @@ __global__ void pack_kernel(PackArgs p) {
         float rh, rl, ih, il;
         split_tf32(re, rh, rl);
         split_tf32(im, ih, il);
-        long long plane_b = (long long)p.Rp * p.Kp * b;
+        const long long row = (p.embed ? 2LL * r : (long long)r) + bi * p.rb_i + bo * p.rb_o;
+        const long long o0 = row * p.pitch + p.k_off + 2LL * k;
         if (p.embed) {
-            long long o0 = plane_b + (long long)(2 * r) * p.Kp + 2 * k;
-            long long o1 = o0 + p.Kp;
+            const long long o1 = o0 + p.pitch;
             *reinterpret_cast<float2*>(p.hi + o0) = make_float2(rh, -ih);
             *reinterpret_cast<float2*>(p.hi + o1) = make_float2(ih, rh);
             *reinterpret_cast<float2*>(p.lo + o0) = make_float2(rl, -il);
             *reinterpret_cast<float2*>(p.lo + o1) = make_float2(il, rl);
         } else {
-            long long o0 = plane_b + (long long)r * p.Kp + 2 * k;
             *reinterpret_cast<float2*>(p.hi + o0) = make_float2(rh, ih);
             *reinterpret_cast<float2*>(p.lo + o0) = make_float2(rl, il);
         }
@@ -285,10 +276,9 @@ constexpr int GEMM_THREADS = DRAIN_THREADS + 64;
 
 struct EpiArgs {
     cplx* C;
-    long long c_m, c_n, c_bi, c_bo;
-    int M, N, Bi;
-    int swapped;          // P side holds the columns n of C (C^T computed)
-    int Pp, Qp;           // packed-row stride per batch of P and Q (0 if shared)
+    long long c_p, c_q, c_bi, c_bo;   // output strides of P row p, Q row q, batch (bi, bo)
+    int Pn, Qn, Bi;       // valid complex rows of P and Q; inner batch extent
+    long long p_sbi, p_sbo, q_sbi, q_sbo;   // real-row offset of batch (bi, bo) in P / Q (0: shared)
     int nkb;              // K' / BK
     int n_ptiles, n_qtiles, batches;   // tile grid; tile t: P tile fastest, then Q tile, then batch
     cplx alpha, beta;
@@ -297,8 +287,32 @@ struct EpiArgs {
     int q_fast;           // tile order inside a batch: Q tiles fastest (else P tiles fastest)
     int nsplit;           // K ranges per output tile (split-K); > 1: partial results go to W
     int cps;              // chunks per K range
-    cplx* W;              // nsplit x batches x N x M partial results (column-major per batch)
+    cplx* W;              // nsplit x batches x Qn x Pn partial results (P row fastest)
+    unsigned long long stall_ns;   // test hook: > 0 makes the drain warps wait this long on a
+                                   // barrier nothing arrives at, so the launch aborts as on a timeout
+    // packed output (o_hi != nullptr): TF32 hi/lo planes at float2 position
+    // (p % pd)*sp1 + (p / pd)*sp2 + (q % qd)*sq1 + (q / qd)*sq2 + bi*sbi + bo*sbo
+    float* o_hi;
+    float* o_lo;
+    int o_pd, o_qd;
+    long long o_sp1, o_sp2, o_sq1, o_sq2, o_sbi, o_sbo;
 };
+
+// Round a float to TF32 (10 mantissa bits, to nearest, ties to even) with
+// integer operations; inf/nan unchanged.
+__device__ __forceinline__ float tf32_rne(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7F800000u) == 0x7F800000u) return x;
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xFFFFE000u);
+}
+
+// (hi + lo) as a float-float sum -> TF32 pair (th, tl) with
+// |hi + lo - th - tl| <~ 2^-22 |hi + lo|, FP32 and integer operations only.
+__device__ __forceinline__ void ff_to_tf32_pair(float hi, float lo, float& th, float& tl) {
+    th = tf32_rne(hi);
+    tl = tf32_rne(__fadd_rn(__fsub_rn(hi, th), lo));
+}
 
 // double(f) built from f's bits with integer operations (GB300's FP64 pipe is
 // ~64x slower than its integer pipe; conversions would go through it).
@@ -332,7 +346,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     uint64_t* tfull = empty + STAGES;      // [NBUF] chunk accumulated in TMEM buffer b
     uint64_t* tempty = tfull + NBUF;       // [NBUF] buffer b drained
     uint64_t* mdone = tempty + NBUF;       // all MMAs of this CTA complete
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+    uint64_t* stallbar = mdone + 1;        // test hook: never arrived at
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(stallbar + 1);
 
     // an earlier launch on this workspace gave up: do nothing (the host
     // reports the error at its next check)
@@ -376,6 +391,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             mbar_init(&tempty[i], DRAIN_THREADS);
         }
         mbar_init(mdone, 1);
+        mbar_init(stallbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -396,7 +412,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 int pt, qt, b, ks;
                 tile_of(t, pt, qt, b, ks);
-                const int prow0 = b * ea.Pp + pt * BM, qrow0 = b * ea.Qp + qt * BN;
+                const int bi = b % ea.Bi, bo = b / ea.Bi;
+                const int prow0 = (int)(bi * ea.p_sbi + bo * ea.p_sbo) + pt * BM;
+                const int qrow0 = (int)(bi * ea.q_sbi + bo * ea.q_sbo) + qt * BN;
                 int c0, c1;
                 krange(t, c0, c1);
                 const int kb1 = min(ea.nkb, c1 * CHUNK_KB);
@@ -470,6 +488,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const bool beta0 = (ea.beta.x == 0.0 && ea.beta.y == 0.0);
         unsigned cg = 0;
         bool ok = true;
+        // test hook: a wait that runs out (nothing arrives at stallbar); the
+        // other roles see the error flag and abort as after a real timeout
+        if (ea.stall_ns > 0 && !mbar_wait(stallbar, 0, ea.err, ea.stall_ns)) ok = false;
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int pt, qt, b, ks;
             tile_of(t, pt, qt, b, ks);
@@ -500,43 +521,60 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             }
             if (!ok) break;
             const int trow = quad * 32 + lane;                  // row of C~ inside the tile
-            const int pr = pt * BM + trow;                      // complex row of P
+            const int p = pt * BM + trow;                       // complex row of P
             const int bi = b % ea.Bi, bo = b / ea.Bi;
-            cplx* C = ea.C + bi * ea.c_bi + bo * ea.c_bo;
-            // split-K: this K range's partial sum, dense column-major, plain store
-            cplx* Wt = ea.nsplit > 1 ? ea.W + ((long long)ks * ea.batches + b) * ea.M * (long long)ea.N : nullptr;
+            // split-K: this K range's partial sum, dense (P row fastest), plain store
+            cplx* Wt = ea.nsplit > 1 ? ea.W + ((long long)ks * ea.batches + b) * ea.Pn * (long long)ea.Qn : nullptr;
             // columns 2q and 2q + 1 of C~ hold the real and imaginary parts of
             // one entry (the Q side carries the real embedding), so each
             // thread owns whole complex outputs
+            if (p < ea.Pn) {
+                if (ea.o_hi) {
+                    // packed output: TF32 planes for a later contraction, no FP64
+                    const long long pbase = (long long)(p % ea.o_pd) * ea.o_sp1 + (long long)(p / ea.o_pd) * ea.o_sp2 +
+                                            bi * ea.o_sbi + bo * ea.o_sbo;
 #pragma unroll
-            for (int j = 0; j < DCOLS; j += 2) {
-                const int qn = (qt * BN + col0 + j) >> 1;       // complex row of Q = the other index
-                const int m = ea.swapped ? qn : pr;
-                const int n = ea.swapped ? pr : qn;
-                if (m >= ea.M || n >= ea.N) continue;
-                const double re = f32_to_f64(hi[j]) + f32_to_f64(lo[j]);
-                const double im = f32_to_f64(hi[j + 1]) + f32_to_f64(lo[j + 1]);
-                if (Wt) {
-                    Wt[m + (long long)n * ea.M] = make_double2(re, im);
+                    for (int j = 0; j < DCOLS; j += 2) {
+                        const int q = (qt * BN + col0 + j) >> 1;
+                        if (q >= ea.Qn) continue;
+                        const long long pos = pbase + (long long)(q % ea.o_qd) * ea.o_sq1 + (long long)(q / ea.o_qd) * ea.o_sq2;
+                        float rh, rl, ih, il;
+                        ff_to_tf32_pair(hi[j], lo[j], rh, rl);
+                        ff_to_tf32_pair(hi[j + 1], lo[j + 1], ih, il);
+                        reinterpret_cast<float2*>(ea.o_hi)[pos] = make_float2(rh, ih);
+                        reinterpret_cast<float2*>(ea.o_lo)[pos] = make_float2(rl, il);
+                    }
                     continue;
                 }
-                cplx* cp = C + m * ea.c_m + n * ea.c_n;
-                cplx r;
-                if (ea.mode == 0) {                 // alpha = 1, beta = 0
-                    r = make_double2(re, im);
-                } else if (ea.mode == 1) {          // alpha = 1, beta = 1
-                    cplx o = *cp;
-                    r = make_double2(o.x + re, o.y + im);
-                } else {
-                    r.x = ea.alpha.x * re - ea.alpha.y * im;
-                    r.y = ea.alpha.x * im + ea.alpha.y * re;
-                    if (!beta0) {
-                        cplx o = *cp;
-                        r.x += ea.beta.x * o.x - ea.beta.y * o.y;
-                        r.y += ea.beta.x * o.y + ea.beta.y * o.x;
+                cplx* C = ea.C + bi * ea.c_bi + bo * ea.c_bo + p * ea.c_p;
+#pragma unroll
+                for (int j = 0; j < DCOLS; j += 2) {
+                    const int q = (qt * BN + col0 + j) >> 1;       // complex row of Q
+                    if (q >= ea.Qn) continue;
+                    const double re = f32_to_f64(hi[j]) + f32_to_f64(lo[j]);
+                    const double im = f32_to_f64(hi[j + 1]) + f32_to_f64(lo[j + 1]);
+                    if (Wt) {
+                        Wt[p + (long long)q * ea.Pn] = make_double2(re, im);
+                        continue;
                     }
+                    cplx* cp = C + q * ea.c_q;
+                    cplx r;
+                    if (ea.mode == 0) {                 // alpha = 1, beta = 0
+                        r = make_double2(re, im);
+                    } else if (ea.mode == 1) {          // alpha = 1, beta = 1
+                        cplx o = *cp;
+                        r = make_double2(o.x + re, o.y + im);
+                    } else {
+                        r.x = ea.alpha.x * re - ea.alpha.y * im;
+                        r.y = ea.alpha.x * im + ea.alpha.y * re;
+                        if (!beta0) {
+                            cplx o = *cp;
+                            r.x += ea.beta.x * o.x - ea.beta.y * o.y;
+                            r.y += ea.beta.x * o.y + ea.beta.y * o.x;
+                        }
+                    }
+                    *cp = r;
                 }
-                *cp = r;
             }
         }
     }
@@ -550,20 +588,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
 // C = alpha sum_ks W[ks] + beta C, summing the K ranges in increasing order.
 __global__ void splitk_reduce_kernel(EpiArgs ea) {
-    const long long MN = (long long)ea.M * ea.N, total = MN * ea.batches;
+    const long long PQ = (long long)ea.Pn * ea.Qn, total = PQ * ea.batches;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(e / MN);
-        const long long mn = e - b * MN;
-        const int m = (int)(mn % ea.M), n = (int)(mn / ea.M);
-        cplx acc = ea.W[(long long)b * MN + mn];
+        const int b = (int)(e / PQ);
+        const long long pq = e - b * PQ;
+        const int p = (int)(pq % ea.Pn), q = (int)(pq / ea.Pn);
+        cplx acc = ea.W[(long long)b * PQ + pq];
         for (int ks = 1; ks < ea.nsplit; ++ks) {
-            cplx w = ea.W[((long long)ks * ea.batches + b) * MN + mn];
+            cplx w = ea.W[((long long)ks * ea.batches + b) * PQ + pq];
             acc.x += w.x;
             acc.y += w.y;
         }
         const int bi = b % ea.Bi, bo = b / ea.Bi;
-        cplx* cp = ea.C + bi * ea.c_bi + bo * ea.c_bo + m * ea.c_m + n * ea.c_n;
+        cplx* cp = ea.C + bi * ea.c_bi + bo * ea.c_bo + p * ea.c_p + q * ea.c_q;
         cplx r;
         if (ea.mode == 0) {
             r = acc;
@@ -584,15 +622,34 @@ __global__ void splitk_reduce_kernel(EpiArgs ea) {
 }
 
 // ------------------------------------------------------------------- host
+// Per-device state of the host side: SM count and whether the kernel's
+// shared-memory attribute has been raised (both are properties of a device,
+// so a process that drives several GPUs keeps one entry per device).
+constexpr int MAX_DEVICES = 64;
+struct DeviceState {
+    int n_sm = 0;
+    bool attr_set = false;
+};
+DeviceState g_dev[MAX_DEVICES];
+std::mutex g_dev_mu;
+
+DeviceState& device_state() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= MAX_DEVICES) dev = 0;
+    return g_dev[dev];
+}
+
 int num_sms() {
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
+    DeviceState& d = device_state();
+    if (d.n_sm == 0) {
+        std::lock_guard<std::mutex> lock(g_dev_mu);
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (n_sm <= 0) n_sm = 1;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        d.n_sm = n > 0 ? n : 1;
     }
-    return n_sm;
+    return d.n_sm;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -609,32 +666,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* m, float* base, long long rows, int kp, int box_rows) {
+// 2-D map over `rows` rows of `kp` floats, rows `pitch` floats apart.
+bool make_map(CUtensorMap* m, const float* base, long long rows, int kp, long long pitch, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kp * 4};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
     cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
-
-struct Plan {
-    bool ok = false;
-    bool swapped = false;
-    bool p_bcast = false, q_bcast = false;   // operand identical in every batch: packed once
-    int Rp_rows = 0, Rq_rows = 0;    // complex rows of P and Q
-    int Pp = 0, Qp = 0, Kp = 0;      // padded real rows / K'
-    long long batches = 0;
-    int nsplit = 1, cps = 0;         // split-K: K ranges per tile, chunks per range
-    size_t w_off = 0;                // byte offset of the partial results
-    size_t bytes = 0;
-};
 
 // Split-K: the number of K ranges that minimises the modelled makespan,
 // waves x (chunks per range + SPLIT_EPI_CHUNKS), where a wave is one work
@@ -644,34 +690,13 @@ struct Plan {
 constexpr int SPLIT_MIN_CHUNKS = 4;
 constexpr int SPLIT_EPI_CHUNKS = 4;
 
-Plan plan_for(const GemmArgs& g, int max_split) {
-    Plan pl;
-    long long K = (long long)g.Ki * g.Ko;
-    if (g.M <= 0 || g.N <= 0 || K < 16) return pl;
-    if (std::min(g.M, g.N) < 16 || std::max(g.M, g.N) < 64) return pl;
-    // P: one real row per complex row; Q: the real embedding (two real rows
-    // per complex row).  The doubled side is the one whose packed bytes cost
-    // less -- rows times the batches it is packed for (1 if all batches share
-    // it) -- and on a tie the smaller side.
-    pl.batches = (long long)g.Bi * g.Bo;
-    const bool a_b = (g.a_bi == 0 || g.Bi == 1) && (g.a_bo == 0 || g.Bo == 1);
-    const bool b_b = (g.b_bi == 0 || g.Bi == 1) && (g.b_bo == 0 || g.Bo == 1);
-    const long long ra = (long long)g.M * (a_b ? 1 : pl.batches), rb = (long long)g.N * (b_b ? 1 : pl.batches);
-    const long long cost_a_p = ra + 2 * rb, cost_b_p = rb + 2 * ra;   // P = A side / P = B side
-    pl.swapped = cost_b_p < cost_a_p || (cost_b_p == cost_a_p && g.N > g.M);
-    pl.Rp_rows = pl.swapped ? g.N : g.M;
-    pl.Rq_rows = pl.swapped ? g.M : g.N;
-    pl.Pp = (int)round_up(pl.Rp_rows, BM);
-    pl.Qp = (int)round_up(2LL * pl.Rq_rows, BN);
-    pl.Kp = (int)round_up(2 * K, BK);
-    if (pl.batches > 65535 || pl.Qp / BN > 65535) return pl;
-    pl.p_bcast = pl.swapped ? b_b : a_b;
-    pl.q_bcast = pl.swapped ? a_b : b_b;
-    size_t pe = (size_t)(pl.p_bcast ? 1 : pl.batches) * pl.Pp * pl.Kp;
-    size_t qe = (size_t)(pl.q_bcast ? 1 : pl.batches) * pl.Qp * pl.Kp;
-    pl.bytes = 2 * (pe + qe) * sizeof(float) + 256;
-    const int nchunk = (pl.Kp / BK + CHUNK_KB - 1) / CHUNK_KB;
-    const long long tiles = (long long)(pl.Pp / BM) * (pl.Qp / BN) * pl.batches;
+struct SplitK {
+    int nsplit = 1, cps = 0;
+};
+
+SplitK choose_split(long long tiles, int nkb, int max_split) {
+    SplitK sk;
+    const int nchunk = (nkb + CHUNK_KB - 1) / CHUNK_KB;
     int ns = 1;
     if (max_split > 1) {
         const long long sms = num_sms();
@@ -687,21 +712,196 @@ Plan plan_for(const GemmArgs& g, int max_split) {
                 ns = n;
             }
     }
+    sk.cps = nchunk;
     if (ns > 1) {
-        pl.cps = (nchunk + ns - 1) / ns;
-        pl.nsplit = (nchunk + pl.cps - 1) / pl.cps;
+        sk.cps = (nchunk + ns - 1) / ns;
+        sk.nsplit = (nchunk + sk.cps - 1) / sk.cps;
     }
-    if (pl.nsplit > 1) {
+    return sk;
+}
+
+SplitK mma_split(const SplitMma& m) {
+    const long long tiles = (long long)(m.Pp / BM) * (m.Qp / BN) * m.Bi * (long long)m.Bo;
+    return choose_split(tiles, m.Kp / BK, m.out ? 1 : m.max_split);
+}
+
+// ----------------------------------------------------- legacy GemmArgs plan
+// P: one real row per complex row; Q: the real embedding (two real rows per
+// complex row).  The doubled side is the one whose packed bytes cost less --
+// rows times the batches it is packed for -- and on a tie the smaller side.
+// An operand is packed only for the batch dimensions it varies in.
+struct Plan {
+    bool ok = false;
+    bool swapped = false;            // P = B side (the columns n of C)
+    int Pp = 0, Qp = 0, Kp = 0;      // padded real rows per packed batch / K'
+    int p_vbi = 0, p_vbo = 0, q_vbi = 0, q_vbo = 0;   // side varies with bi / bo
+    long long batches = 0;
+    size_t pe = 0, qe = 0;           // floats per plane of P / Q
+    size_t bytes = 0;                // error flag + planes (+ split-K partials)
+    size_t w_off = 0;
+    SplitMma mma{};
+};
+
+Plan plan_for(const GemmArgs& g, int max_split) {
+    Plan pl;
+    long long K = (long long)g.Ki * g.Ko;
+    if (g.M <= 0 || g.N <= 0 || K < 16) return pl;
+    if (std::min(g.M, g.N) < 16 || std::max(g.M, g.N) < 64) return pl;
+    pl.batches = (long long)g.Bi * g.Bo;
+    const int a_vbi = g.a_bi != 0 && g.Bi > 1, a_vbo = g.a_bo != 0 && g.Bo > 1;
+    const int b_vbi = g.b_bi != 0 && g.Bi > 1, b_vbo = g.b_bo != 0 && g.Bo > 1;
+    const long long na = (a_vbi ? g.Bi : 1) * (long long)(a_vbo ? g.Bo : 1);
+    const long long nb = (b_vbi ? g.Bi : 1) * (long long)(b_vbo ? g.Bo : 1);
+    const long long ra = (long long)g.M * na, rb = (long long)g.N * nb;
+    const long long cost_a_p = ra + 2 * rb, cost_b_p = rb + 2 * ra;   // P = A side / P = B side
+    pl.swapped = cost_b_p < cost_a_p || (cost_b_p == cost_a_p && g.N > g.M);
+    const int Rp_rows = pl.swapped ? g.N : g.M, Rq_rows = pl.swapped ? g.M : g.N;
+    pl.Pp = (int)round_up(Rp_rows, BM);
+    pl.Qp = (int)round_up(2LL * Rq_rows, BN);
+    pl.Kp = (int)round_up(2 * K, BK);
+    if (pl.batches > 65535 || pl.Qp / BN > 65535) return pl;
+    pl.p_vbi = pl.swapped ? b_vbi : a_vbi;
+    pl.p_vbo = pl.swapped ? b_vbo : a_vbo;
+    pl.q_vbi = pl.swapped ? a_vbi : b_vbi;
+    pl.q_vbo = pl.swapped ? a_vbo : b_vbo;
+    const long long np = pl.swapped ? nb : na, nq = pl.swapped ? na : nb;
+    pl.pe = (size_t)np * pl.Pp * pl.Kp;
+    pl.qe = (size_t)nq * pl.Qp * pl.Kp;
+    SplitMma& m = pl.mma;
+    m.Kp = pl.Kp;
+    m.Pn = Rp_rows;
+    m.Qn = Rq_rows;
+    m.Pp = pl.Pp;
+    m.Qp = pl.Qp;
+    m.Bi = g.Bi;
+    m.Bo = g.Bo;
+    m.p_sbi = pl.p_vbi ? pl.Pp : 0;
+    m.p_sbo = pl.p_vbo ? (long long)pl.Pp * (pl.p_vbi ? g.Bi : 1) : 0;
+    m.q_sbi = pl.q_vbi ? pl.Qp : 0;
+    m.q_sbo = pl.q_vbo ? (long long)pl.Qp * (pl.q_vbi ? g.Bi : 1) : 0;
+    m.P_rows = (long long)np * pl.Pp;
+    m.Q_rows = (long long)nq * pl.Qp;
+    m.P_pitch = m.Q_pitch = pl.Kp;
+    m.C = g.C;
+    m.c_p = pl.swapped ? g.c_n : g.c_m;
+    m.c_q = pl.swapped ? g.c_m : g.c_n;
+    m.c_bi = g.c_bi;
+    m.c_bo = g.c_bo;
+    m.alpha = g.alpha;
+    m.beta = g.beta;
+    m.out = nullptr;
+    m.max_split = max_split;
+    const SplitK sk = mma_split(m);
+    pl.bytes = 256 + 2 * (pl.pe + pl.qe) * sizeof(float);
+    if (sk.nsplit > 1) {
         pl.w_off = (pl.bytes + 255) / 256 * 256;
-        pl.bytes = pl.w_off + (size_t)pl.nsplit * pl.batches * g.M * (size_t)g.N * sizeof(cplx);
-    } else {
-        pl.cps = nchunk;
+        pl.bytes = pl.w_off + (size_t)sk.nsplit * pl.batches * g.M * (size_t)g.N * sizeof(cplx);
     }
     pl.ok = true;
     return pl;
 }
 
+SplitPackArgs side_pack_args(const GemmArgs& g, const Plan& pl, int side, float* hi, float* lo) {
+    // side 0 = P, 1 = Q; the A side as (row m, k), the B side as (row n, k)
+    const bool a_side = (side == 0) != pl.swapped;
+    SplitPackArgs p;
+    std::memset(&p, 0, sizeof(p));
+    if (a_side) {
+        p.src = g.A; p.s_r = g.a_m; p.s_ki = g.a_ki; p.s_ko = g.a_ko; p.s_bi = g.a_bi; p.s_bo = g.a_bo;
+        p.R = g.M; p.conj = g.conjA;
+    } else {
+        p.src = g.B; p.s_r = g.b_n; p.s_ki = g.b_ki; p.s_ko = g.b_ko; p.s_bi = g.b_bi; p.s_bo = g.b_bo;
+        p.R = g.N; p.conj = g.conjB;
+    }
+    p.Ki = g.Ki;
+    p.Ko = g.Ko;
+    const int vbi = side == 0 ? pl.p_vbi : pl.q_vbi, vbo = side == 0 ? pl.p_vbo : pl.q_vbo;
+    p.Bi = vbi ? g.Bi : 1;
+    p.Bo = vbo ? g.Bo : 1;
+    p.embed = side;
+    const int rows = side == 0 ? pl.Pp : pl.Qp;
+    p.Rpad = side == 0 ? rows : rows / 2;
+    p.Kc = pl.Kp / 2;
+    p.rb_i = rows;
+    p.rb_o = (long long)rows * p.Bi;
+    p.pitch = pl.Kp;
+    p.k_off = 0;
+    p.hi = hi;
+    p.lo = lo;
+    return p;
+}
+
 }  // namespace
+
+// ------------------------------------------------------------- public API
+int split_pack(const SplitPackArgs& p, cudaStream_t stream) {
+    const long long total = (long long)p.Rpad * p.Kc * p.Bi * p.Bo;
+    if (total <= 0) return 0;
+    const long long grid = std::min<long long>((total + 255) / 256, 152LL * 16);
+    pack_kernel<<<(unsigned)grid, 256, 0, stream>>>(p);
+    return 1;
+}
+
+size_t split_mma_partials(const SplitMma& m) {
+    const SplitK sk = mma_split(m);
+    if (sk.nsplit <= 1) return 0;
+    return (size_t)sk.nsplit * m.Bi * (size_t)m.Bo * m.Pn * (size_t)m.Qn * sizeof(cplx);
+}
+
+int split_mma(const SplitMma& m, int* err_flag, void* partials, size_t partial_bytes, cudaStream_t stream) {
+    if (!err_flag || partial_bytes < split_mma_partials(m) || (split_mma_partials(m) > 0 && !partials)) return -2;
+    if (m.Kp % BK || m.Pp % BM || m.Qp % BN || m.Bi < 1 || m.Bo < 1 || m.Pn < 1 || m.Qn < 1) return -1;
+    {
+        DeviceState& d = device_state();
+        std::lock_guard<std::mutex> lock(g_dev_mu);
+        if (!d.attr_set) {
+            if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+                cudaSuccess)
+                return -1;
+            d.attr_set = true;
+        }
+    }
+    CUtensorMap mPh, mPl, mQh, mQl;
+    if (!make_map(&mPh, m.Ph, m.P_rows, m.Kp, m.P_pitch, BM) || !make_map(&mPl, m.Pl, m.P_rows, m.Kp, m.P_pitch, BM) ||
+        !make_map(&mQh, m.Qh, m.Q_rows, m.Kp, m.Q_pitch, BN) || !make_map(&mQl, m.Ql, m.Q_rows, m.Kp, m.Q_pitch, BN))
+        return -1;
+    const SplitK sk = mma_split(m);
+    EpiArgs ea;
+    std::memset(&ea, 0, sizeof(ea));
+    ea.C = m.C; ea.c_p = m.c_p; ea.c_q = m.c_q; ea.c_bi = m.c_bi; ea.c_bo = m.c_bo;
+    ea.Pn = m.Pn; ea.Qn = m.Qn; ea.Bi = m.Bi;
+    ea.p_sbi = m.p_sbi; ea.p_sbo = m.p_sbo; ea.q_sbi = m.q_sbi; ea.q_sbo = m.q_sbo;
+    ea.nkb = m.Kp / BK;
+    ea.alpha = m.alpha; ea.beta = m.beta;
+    const bool a1 = m.alpha.x == 1.0 && m.alpha.y == 0.0;
+    ea.mode = (a1 && m.beta.x == 0.0 && m.beta.y == 0.0) ? 0 : (a1 && m.beta.x == 1.0 && m.beta.y == 0.0) ? 1 : 2;
+    ea.err = err_flag;
+    ea.nsplit = sk.nsplit;
+    ea.cps = sk.cps;
+    ea.W = sk.nsplit > 1 ? reinterpret_cast<cplx*>(partials) : nullptr;
+    ea.stall_ns = test_take_tc_stall();
+    if (m.out) {
+        ea.o_hi = m.out->hi; ea.o_lo = m.out->lo;
+        ea.o_pd = m.out->pd; ea.o_qd = m.out->qd;
+        ea.o_sp1 = m.out->sp1; ea.o_sp2 = m.out->sp2; ea.o_sq1 = m.out->sq1; ea.o_sq2 = m.out->sq2;
+        ea.o_sbi = m.out->sbi; ea.o_sbo = m.out->sbo;
+    }
+    // persistent: one CTA per SM walks the tiles, the smaller tile count
+    // fastest so that CTAs sharing the other operand's tile run together and
+    // hit it in L2 (an operand larger than L2 is then read about once)
+    ea.n_ptiles = m.Pp / BM;
+    ea.n_qtiles = m.Qp / BN;
+    ea.q_fast = ea.n_qtiles < ea.n_ptiles;
+    ea.batches = m.Bi * m.Bo;
+    const long long ntiles = (long long)ea.n_ptiles * ea.n_qtiles * ea.batches * sk.nsplit;
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms());
+    tc_gemm_kernel<<<grid, GEMM_THREADS, SMEM_BYTES, stream>>>(mPh, mPl, mQh, mQl, ea);
+    if (sk.nsplit == 1) return 1;
+    const long long total = (long long)m.Pn * m.Qn * ea.batches;
+    const unsigned rg = (unsigned)std::min<long long>((total + 255) / 256, (long long)num_sms() * 8);
+    splitk_reduce_kernel<<<rg, 256, 0, stream>>>(ea);
+    return 2;
+}
 
 size_t split_workspace_bytes(const GemmArgs& g, int max_split) {
     Plan pl = plan_for(g, max_split);
@@ -716,37 +916,13 @@ int launch_split_pack(const GemmArgs& g, cudaStream_t stream, void* workspace, s
     Plan pl = plan_for(g, max_split);
     if (!pl.ok || !encode_fn()) return -1;
     if (!workspace || workspace_bytes < pl.bytes) return -2;
-    const long long np_b = pl.p_bcast ? 1 : pl.batches, nq_b = pl.q_bcast ? 1 : pl.batches;
-    size_t pe = (size_t)np_b * pl.Pp * pl.Kp, qe = (size_t)nq_b * pl.Qp * pl.Kp;
     float* Ph = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(workspace) + 256);
-    float* Pl = Ph + pe;
-    float* Qh = Pl + pe;
-    float* Ql = Qh + qe;
-    // A side as (row m, k) and B side as (row n, k)
-    PackArgs pa, pb;
-    std::memset(&pa, 0, sizeof(pa));
-    std::memset(&pb, 0, sizeof(pb));
-    pa.src = g.A; pa.s_r = g.a_m; pa.s_ki = g.a_ki; pa.s_ko = g.a_ko; pa.s_bi = g.a_bi; pa.s_bo = g.a_bo;
-    pa.R = g.M; pa.conj = g.conjA;
-    pb.src = g.B; pb.s_r = g.b_n; pb.s_ki = g.b_ki; pb.s_ko = g.b_ko; pb.s_bi = g.b_bi; pb.s_bo = g.b_bo;
-    pb.R = g.N; pb.conj = g.conjB;
-    for (PackArgs* p : {&pa, &pb}) {
-        p->Ki = g.Ki; p->Ko = g.Ko; p->Bi = g.Bi; p->Bo = g.Bo; p->Kp = pl.Kp;
-    }
-    PackArgs& P = pl.swapped ? pb : pa;
-    PackArgs& Q = pl.swapped ? pa : pb;
-    P.embed = 0; P.Rp = pl.Pp; P.hi = Ph; P.lo = Pl;
-    Q.embed = 1; Q.Rp = pl.Qp; Q.hi = Qh; Q.lo = Ql;
-    if (pl.p_bcast) { P.Bi = 1; P.Bo = 1; }
-    if (pl.q_bcast) { Q.Bi = 1; Q.Bo = 1; }
-    int launches = 0;
-    for (PackArgs* p : {&P, &Q}) {
-        long long total = (long long)(p->embed ? p->Rp / 2 : p->Rp) * (p->Kp / 2) * p->Bi * p->Bo;
-        long long grid = std::min<long long>((total + 255) / 256, 152LL * 16);
-        pack_kernel<<<(unsigned)grid, 256, 0, stream>>>(*p);
-        ++launches;
-    }
-    return launches;
+    float* Pl = Ph + pl.pe;
+    float* Qh = Pl + pl.pe;
+    float* Ql = Qh + pl.qe;
+    int n = split_pack(side_pack_args(g, pl, 0, Ph, Pl), stream);
+    n += split_pack(side_pack_args(g, pl, 1, Qh, Ql), stream);
+    return n;
 }
 
 // Phase 2: the tcgen05 GEMM on the packed operands of the same GemmArgs.
@@ -754,51 +930,16 @@ int launch_split_mma(const GemmArgs& g, cudaStream_t stream, void* workspace, si
                      int max_split) {
     Plan pl = plan_for(g, max_split);
     if (!pl.ok || !workspace || workspace_bytes < pl.bytes) return -1;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        attr_set = true;
-    }
-    const long long pb = pl.p_bcast ? 1 : pl.batches, qb = pl.q_bcast ? 1 : pl.batches;
-    size_t pe = (size_t)pb * pl.Pp * pl.Kp, qe = (size_t)qb * pl.Qp * pl.Kp;
-    int* err = reinterpret_cast<int*>(workspace);          // first 256 bytes: error flag
     float* Ph = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(workspace) + 256);
-    float* Pl = Ph + pe;
-    float* Qh = Pl + pe;
-    float* Ql = Qh + qe;
-    CUtensorMap mPh, mPl, mQh, mQl;
-    if (!make_map(&mPh, Ph, pb * pl.Pp, pl.Kp, BM) || !make_map(&mPl, Pl, pb * pl.Pp, pl.Kp, BM) ||
-        !make_map(&mQh, Qh, qb * pl.Qp, pl.Kp, BN) || !make_map(&mQl, Ql, qb * pl.Qp, pl.Kp, BN))
-        return -1;
-    EpiArgs ea;
-    ea.C = g.C; ea.c_m = g.c_m; ea.c_n = g.c_n; ea.c_bi = g.c_bi; ea.c_bo = g.c_bo;
-    ea.M = g.M; ea.N = g.N; ea.Bi = g.Bi;
-    ea.swapped = pl.swapped;
-    ea.Pp = pl.p_bcast ? 0 : pl.Pp;   // batch stride of the packed rows (0: shared)
-    ea.Qp = pl.q_bcast ? 0 : pl.Qp;
-    ea.nkb = pl.Kp / BK;
-    ea.alpha = g.alpha; ea.beta = g.beta;
-    const bool a1 = g.alpha.x == 1.0 && g.alpha.y == 0.0;
-    ea.mode = (a1 && g.beta.x == 0.0 && g.beta.y == 0.0) ? 0 : (a1 && g.beta.x == 1.0 && g.beta.y == 0.0) ? 1 : 2;
-    ea.err = err;
-    ea.nsplit = pl.nsplit;
-    ea.cps = pl.cps;
-    ea.W = pl.nsplit > 1 ? reinterpret_cast<cplx*>(reinterpret_cast<uint8_t*>(workspace) + pl.w_off) : nullptr;
-    // persistent: one CTA per SM walks the tiles, the smaller tile count
-    // fastest so that CTAs sharing the other operand's tile run together and
-    // hit it in L2 (an operand larger than L2 is then read about once)
-    ea.n_ptiles = pl.Pp / BM;
-    ea.n_qtiles = pl.Qp / BN;
-    ea.q_fast = ea.n_qtiles < ea.n_ptiles;
-    ea.batches = (int)pl.batches;
-    long long ntiles = (long long)ea.n_ptiles * ea.n_qtiles * pl.batches * pl.nsplit;
-    unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms());
-    tc_gemm_kernel<<<grid, GEMM_THREADS, SMEM_BYTES, stream>>>(mPh, mPl, mQh, mQl, ea);
-    if (pl.nsplit == 1) return 1;
-    long long total = (long long)g.M * g.N * pl.batches;
-    unsigned rg = (unsigned)std::min<long long>((total + 255) / 256, (long long)num_sms() * 8);
-    splitk_reduce_kernel<<<rg, 256, 0, stream>>>(ea);
-    return 2;
+    float* Pl = Ph + pl.pe;
+    float* Qh = Pl + pl.pe;
+    float* Ql = Qh + pl.qe;
+    SplitMma m = pl.mma;
+    m.Ph = Ph; m.Pl = Pl; m.Qh = Qh; m.Ql = Ql;
+    void* partials = pl.w_off ? reinterpret_cast<uint8_t*>(workspace) + pl.w_off : nullptr;
+    const size_t pbytes = pl.w_off ? workspace_bytes - pl.w_off : 0;
+    int r = split_mma(m, reinterpret_cast<int*>(workspace), partials, pbytes, stream);
+    return r < 0 ? -1 : r;
 }
 
 int launch_zgemm_split(const GemmArgs& g, cudaStream_t stream, void* workspace, size_t workspace_bytes) {

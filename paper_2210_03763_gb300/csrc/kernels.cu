@@ -218,8 +218,10 @@ __device__ void tridiag_expm_warp(const double* a, const double* b, int m, doubl
     double rs = fabs(ai) + fabs(bl) + fabs(bu);
     for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, o));
     double zn = sqrt(zr * zr + zi * zi);
-    int nsub = (int)ceil(zn * rs / 0.5);
-    if (nsub < 1) nsub = 1;
+    // substeps: bounded also for non-finite or absurd norms (a NaN state is
+    // reported through the nonfinite flag, never by a runaway loop)
+    const double want = zn * rs / 0.5;
+    int nsub = (want >= 1.0 && want < 65536.0) ? (int)ceil(want) : (want >= 65536.0 ? 65536 : 1);
     double hr = zr / nsub, hi = zi / nsub;
     cplx u = make_double2(l == 0 ? 1.0 : 0.0, 0.0);
     for (int s = 0; s < nsub; ++s) {
@@ -358,6 +360,84 @@ __global__ void check_finite_kernel(const cplx* x, long long n, int* flag) {
     }
 }
 
+// G_i = sum_j W[j + nb*i] N_j for i < r (real weights, complex matrices of n
+// entries each, stacked contiguously): the channel operators
+// G_i = sum_j V_ij n_j of an effective Hamiltonian.  One thread per matrix
+// entry keeps up to 16 outputs in registers and reads each N_j entry once per
+// group of 16 outputs (memory bound for the few outputs of a group).
+constexpr int WSUM_GROUP = 16;
+__global__ void weighted_sum_kernel(const cplx* __restrict__ N, int nb, long long n, const double* __restrict__ W,
+                                    int r, cplx* __restrict__ G, int staged) {
+    extern __shared__ double sw_smem[];
+    const double* sw = W;   // weights from global memory unless they fit in shared memory
+    if (staged) {
+        for (int i = threadIdx.x; i < nb * r; i += blockDim.x) sw_smem[i] = W[i];
+        __syncthreads();
+        sw = sw_smem;
+    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        for (int i0 = 0; i0 < r; i0 += WSUM_GROUP) {
+            cplx acc[WSUM_GROUP];
+#pragma unroll
+            for (int t = 0; t < WSUM_GROUP; ++t) acc[t] = make_double2(0.0, 0.0);
+            for (int j = 0; j < nb; ++j) {
+                const cplx v = N[(long long)j * n + e];
+#pragma unroll
+                for (int t = 0; t < WSUM_GROUP; ++t) {
+                    if (i0 + t < r) {
+                        const double w = sw[j + nb * (i0 + t)];
+                        acc[t].x = fma(w, v.x, acc[t].x);
+                        acc[t].y = fma(w, v.y, acc[t].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < WSUM_GROUP; ++t)
+                if (i0 + t < r) G[(long long)(i0 + t) * n + e] = acc[t];
+        }
+    }
+}
+
+// FP64 throughput probes: many independent FMA chains per thread (the FP64
+// ALU, DFMA), or chains of FP64 tensor-core instructions (DMMA,
+// mma.sync m8n8k4 f64; four independent accumulators per warp).  The result
+// is stored only under a condition that never holds, which keeps the
+// compiler from removing the chains.
+constexpr int PROBE_CHAINS = 8;
+__global__ void fp64_fma_probe_kernel(double* out, int iters) {
+    double a[PROBE_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) a[k] = 1e-9 * (threadIdx.x + k);
+    const double b = 0.999999999, c = 1e-12;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < PROBE_CHAINS; ++k) a[k] = fma(a[k], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) s += a[k];
+    if (s == 12345.678) out[0] = s;
+}
+
+__global__ void dmma_probe_kernel(double* out, int iters) {
+    const double a = 1e-9 * (threadIdx.x & 31), b = 0.5;
+    double d[4][2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k][0] = d[k][1] = 0.0;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                         : "+d"(d[k][0]), "+d"(d[k][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += d[k][0] + d[k][1];
+    if (s == 12345.678) out[0] = s;
+}
+
 inline int grid_for(long long n) {
     long long g = (n + 255) / 256;
     if (g > 4 * 152) g = 4 * 152;
@@ -456,5 +536,25 @@ int k_assemble_block(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsite
 int k_check_finite(const cplx* x, long long n, int* flag, cudaStream_t s) {
     if (n <= 0) return 0;
     check_finite_kernel<<<grid_for(n), 256, 0, s>>>(x, n, flag);
+    return 1;
+}
+
+// FP64 peak probe (method 0: DFMA chains, 1: DMMA m8n8k4): launches one probe
+// over `blocks` blocks of 256 threads and returns its flop count; the caller
+// times it.  2 flops per FMA; 2 * 8 * 8 * 4 flops per warp-wide DMMA.
+double k_fp64_probe(int method, int blocks, int iters, double* out, cudaStream_t s) {
+    if (method == 0) {
+        fp64_fma_probe_kernel<<<blocks, 256, 0, s>>>(out, iters);
+        return 2.0 * PROBE_CHAINS * (double)iters * 256.0 * blocks;
+    }
+    dmma_probe_kernel<<<blocks, 256, 0, s>>>(out, iters);
+    return 512.0 * 4.0 * (double)iters * (256.0 / 32.0) * blocks;
+}
+
+int k_weighted_sum(const cplx* N, int nb, long long n, const double* W, int r, cplx* G, cudaStream_t s) {
+    if (n <= 0 || r <= 0) return 0;
+    const size_t need = sizeof(double) * (size_t)nb * r;
+    const int staged = need <= 48 * 1024;
+    weighted_sum_kernel<<<grid_for(n), 256, staged ? need : 0, s>>>(N, nb, n, W, r, G, staged);
     return 1;
 }

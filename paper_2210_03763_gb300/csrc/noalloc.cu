@@ -54,17 +54,35 @@ extern "C" ttn_status ttn_contract_split_noalloc(const double* A, const double* 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     size_t need = split_workspace_bytes(g, 1);   // no split-K: the scratch size rule stays as documented
     if (need > NOALLOC_SCRATCH_BYTES) return TTN_ERR_ARG;   // beyond the fixed scratch
-    if (need == 0) {
-        // too small for the tensor-core tiles: the FP64 kernel needs no scratch
-        launch_zgemm_f64(g, s);
-        return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ERR_CUDA;
-    }
     void* scratch = nullptr;
-    ttn_status st = scratch_for_current_device(&scratch);
-    if (st != TTN_OK) return st;
-    // the error flag at the start of the scratch must start at zero
-    if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess) return TTN_ERR_CUDA;
-    if (launch_split_pack(g, s, scratch, NOALLOC_SCRATCH_BYTES, 1) < 0) return TTN_ERR_ARG;
+    int packed = -1;
+    if (need > 0) {
+        ttn_status st = scratch_for_current_device(&scratch);
+        if (st != TTN_OK) return st;
+        // the error flag at the start of the scratch must start at zero
+        if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess) return TTN_ERR_CUDA;
+        packed = launch_split_pack(g, s, scratch, NOALLOC_SCRATCH_BYTES, 1);
+        if (packed == -2) return TTN_ERR_ARG;
+    }
+    if (packed < 0) {
+        // too small for the tensor-core tiles, or no tensor-map encoder in
+        // this driver: the FP64 kernel needs no scratch
+        launch_zgemm_f64(g, s);
+        if (cudaGetLastError() != cudaSuccess) return TTN_ERR_CUDA;
+        return cudaStreamSynchronize(s) == cudaSuccess ? TTN_OK : TTN_ERR_CUDA;
+    }
     if (launch_split_mma(g, s, scratch, NOALLOC_SCRATCH_BYTES, 1) < 0) return TTN_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? TTN_OK : TTN_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return TTN_ERR_CUDA;
+    // a pipeline wait that gave up sets the first word of the scratch: read
+    // it once the contraction is done, and clear it for the next call
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, scratch, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return TTN_ERR_CUDA;
+    if (flag) {
+        if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            return TTN_ERR_CUDA;
+        return TTN_ERR_TIMEOUT;
+    }
+    return TTN_OK;
 }

@@ -1088,7 +1088,17 @@ __global__ void __launch_bounds__(SC_THREADS) sc_select_kernel(const cplx* A, lo
                 }
                 __syncthreads();
             }
+            // non-finite residuals (a NaN matrix) select nothing above: take the
+            // first unused candidate so every index stays in bounds; the NaN
+            // then propagates to the result, where the caller detects it
             chosen = sbi;
+            if (chosen < 0)
+                for (int q = 0; q < ncand; ++q)
+                    if (!cand_used[q]) {
+                        chosen = q;
+                        break;
+                    }
+            if (chosen < 0) chosen = 0;
             res = sc_residual(A, M, kept, r, cand[chosen], Mi, w, y, red);
             p = ncand;   // residuals only decrease: no later scan can reach 1/4 either
         } else {

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -146,7 +147,7 @@ struct ttn_ctx {
 
     std::vector<Env> up, down, phys;
     Env dummy;
-    std::map<std::pair<const Env*, const Env*>, cplx*> vsub;   // G-stack GEMM operands
+    std::map<std::pair<const Env*, const Env*>, double*> vsub;   // G-stack weights
 
     // kernel-level profile: event pairs around launches while enabled
     bool profiling = false;
@@ -157,16 +158,52 @@ struct ttn_ctx {
     size_t ev_next = 0;
     void* split_ws = nullptr;   // packed operands of the split GEMM (+ error flag)
     size_t split_cap = 0;
+    // split-precision H_eff of one node visit (see SplitHeff): per leg the
+    // stacked operand planes [X | channel stacks] and the operator stack,
+    // per channel pair the packed G stack; grown on demand, zeroed when
+    // allocated so that every float the MMAs can read is finite
+    float* shP[3] = {nullptr, nullptr, nullptr};
+    size_t shP_cap[3] = {0, 0, 0};
+    float* shQ[3] = {nullptr, nullptr, nullptr};
+    size_t shQ_cap[3] = {0, 0, 0};
+    float* shG[3] = {nullptr, nullptr, nullptr};
+    size_t shG_cap[3] = {0, 0, 0};
     int64_t stats[6] = {0, 0, 0, 0, 0, 0};
     double max_err = 0.0;
     std::vector<void*> allocs;
 };
+
+// ---- test hooks (ttn_test_inject): host-side fault injection ----------------
+static std::atomic<long long> g_inj_tc_stall{0};     // tensor-core launches still to stall
+static std::atomic<int> g_inj_mmax{0};               // Krylov dimension cap, 0: KRYLOV_MMAX
+static std::atomic<long long> g_inj_alloc_fail{0};   // device allocations still to fail
+constexpr unsigned long long INJ_STALL_NS = 1000000ull;   // 1 ms wait that runs out
+
+namespace {
+
+// Take one unit from a pending-count hook (false when none is pending).
+bool take_one(std::atomic<long long>& n) {
+    long long v = n.load();
+    while (v > 0)
+        if (n.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
+}  // namespace
+
+unsigned long long test_take_tc_stall() { return take_one(g_inj_tc_stall) ? INJ_STALL_NS : 0ull; }
+int test_krylov_mmax() {
+    const int m = g_inj_mmax.load();
+    return (m >= 1 && m < KRYLOV_MMAX) ? m : KRYLOV_MMAX;
+}
+bool test_take_alloc_fail() { return take_one(g_inj_alloc_fail); }
 
 namespace {
 
 void* dalloc(ttn_ctx* c, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (test_take_alloc_fail()) throw TtnError(TTN_ERR_ALLOC, "cudaMalloc: injected failure");
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) throw TtnError(TTN_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     c->allocs.push_back(p);
@@ -196,7 +233,8 @@ void grow_split_ws(ttn_ctx* c, size_t bytes) {
         c->split_cap = 0;
     }
     size_t cap = bytes + bytes / 4;
-    if (cudaMalloc(&c->split_ws, cap) != cudaSuccess) throw TtnError(TTN_ERR_ALLOC, "split workspace");
+    if (test_take_alloc_fail() || cudaMalloc(&c->split_ws, cap) != cudaSuccess)
+        throw TtnError(TTN_ERR_ALLOC, "split workspace");
     CUDA_OK(cudaMemcpy(c->split_ws, &flag, sizeof(int), cudaMemcpyHostToDevice));
     c->split_cap = cap;
 }
@@ -405,32 +443,29 @@ const Env& env_of(ttn_ctx* c, int k, int leg) {
     return ch >= 0 ? c->up[ch] : c->phys[-ch - 1];
 }
 
-cplx* vsub_for(ttn_ctx* c, const Env& a, const Env& b) {
+double* vsub_for(ttn_ctx* c, const Env& a, const Env& b) {
     auto key = std::make_pair(&a, &b);
     auto it = c->vsub.find(key);
     if (it != c->vsub.end()) return it->second;
-    // B operand of the G-stack GEMM: |S_b| x |S_a|, element (j, i) = V(a_i, b_j)
+    // weights of the G stack: |S_b| x |S_a|, element (j, i) = V(a_i, b_j)
     size_t nb = b.sites.size(), na = a.sites.size();
-    std::vector<cplx> h(nb * na);
+    std::vector<double> h(nb * na);
     for (size_t i = 0; i < na; ++i)
-        for (size_t j = 0; j < nb; ++j) h[j + nb * i] = C(c->V[(size_t)a.sites[i] * c->N + b.sites[j]]);
-    cplx* d = (cplx*)dalloc(c, sizeof(cplx) * h.size());
-    CUDA_OK(cudaMemcpy(d, h.data(), sizeof(cplx) * h.size(), cudaMemcpyHostToDevice));
+        for (size_t j = 0; j < nb; ++j) h[j + nb * i] = c->V[(size_t)a.sites[i] * c->N + b.sites[j]];
+    double* d = (double*)dalloc(c, sizeof(double) * std::max<size_t>(1, h.size()));
+    if (!h.empty()) CUDA_OK(cudaMemcpy(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
     c->vsub[key] = d;
     return d;
 }
 
-// G_i = sum_j V_ij n_j^(b) for every atom i of env a, into Gbuf
+// G_i = sum_j V_ij n_j^(b) for every atom i of env a, into Gbuf (a weighted
+// sum of the n stack: memory and FP64 bound, no contraction needed)
 void build_G(ttn_ctx* c, const Env& a, const Env& b, cplx* G) {
     int r = (int)a.sites.size(), nbs = (int)b.sites.size();
     long long DD = (long long)b.D * b.D;
-    GemmArgs g = base_args();
-    g.M = (int)DD; g.N = r; g.Ki = nbs;
-    g.A = b.nops; g.a_m = 1; g.a_ki = DD;
-    g.B = vsub_for(c, a, b); g.b_ki = 1; g.b_n = nbs;
-    g.C = G; g.c_m = 1; g.c_n = DD;
-    ProfScope ps(c, PK_F64, gemm_flops(g), 0.0, &g);
-    c->stats[3] += launch_zgemm_f64(g, c->stream);   // tiny, keep FP64
+    ProfScope ps(c, PK_F64, 4.0 * r * (double)nbs * DD, 0.0);
+    ps.shape[0] = (int)DD; ps.shape[1] = r; ps.shape[2] = nbs; ps.shape[3] = 1;
+    c->stats[3] += k_weighted_sum(b.nops, nbs, DD, vsub_for(c, a, b), r, G, c->stream);
 }
 
 // Pairs of an effective Hamiltonian over envs e[0..2]; G stacks built.
@@ -478,6 +513,300 @@ void heff_apply(ttn_ctx* c, const int* d, cplx* const* hb, const int* Dl, const 
     if (beta == 0.0) c->stats[3] += k_fill(Y, s, C(0.0), c->stream);
 }
 
+// ------------------------------------------- split-precision H_eff (a8)
+// H_eff X in split precision with every operand packed once per use:
+//   per leg u a stacked operand  P_u = [X | Z^(p) for each pair p with a = u]
+//   (rows: the other two legs; K: the leg-u index and, per pair, the channel
+//   index) and the operator stack  Q_u = [H_block(u) | n_1 .. n_r of each
+//   pair]  (packed once per Krylov run), so that
+//     H_eff X = sum_u Q_u x_u P_u
+//   is one long-K contraction per leg.  The channel intermediates
+//   Z_i = G_i x_b X are contractions whose epilogue writes TF32 planes
+//   straight into the K slots of P_a (no FP64 round trip through HBM), and X
+//   is packed once per leg per matvec.  Row layouts of P_u:
+//     u = 0: row b + d1 c;  u = 1: row a + Pp_1 c (batch c);  u = 2: row a + d0 b.
+long long grow_zeroed(ttn_ctx* c, float*& buf, size_t& cap, size_t bytes) {
+    if (bytes <= cap) return 0;
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    if (buf) cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    size_t want = bytes + bytes / 8;
+    if (test_take_alloc_fail() || cudaMalloc(&buf, want) != cudaSuccess) {
+        buf = nullptr;
+        throw TtnError(TTN_ERR_ALLOC, "split operand planes");
+    }
+    CUDA_OK(cudaMemsetAsync(buf, 0, want, c->stream));
+    cap = want;
+    return 1;
+}
+
+struct SplitHeff {
+    struct Leg {
+        bool on = false;      // X is packed on this leg (it has terms or feeds a channel)
+        bool terms = false;   // the leg carries a block term or channel sums
+        int d = 0;            // leg dimension
+        int Pn = 0, Pp = 0;   // valid / padded P rows per batch
+        int nb = 1;           // row batches (d2 for leg 1)
+        long long rows = 0;   // P rows in the planes
+        int Kc = 0, Kp = 0;   // complex K of the stack, floats per row
+        int Qrows = 0;        // padded real rows of the operator stack
+        int nslots = 0;       // complex K used so far while laying out
+        float *Ph = nullptr, *Pl = nullptr, *Qh = nullptr, *Ql = nullptr;
+    } leg[3];
+    struct PairPlan {
+        int a, b, r;
+        long long base;       // complex K offset of the pair's slot in P_a
+        int Kz;               // K' of the G contraction (floats)
+        int Qrows;            // padded real rows of one G matrix
+        float *Gh = nullptr, *Gl = nullptr;
+    } pp[3];
+    int np = 0;
+    int d[3] = {0, 0, 0};
+    bool ok = false;
+};
+
+bool split_heff_prepare(ttn_ctx* c, SplitHeff& S, const int* d, cplx* const* hb, const Pair* pairs, int np) {
+    S = SplitHeff();
+    if (c->prec != TTN_SPLIT_TF32X3 || g_force_fp64) return false;
+    for (int u = 0; u < 3; ++u) S.d[u] = d[u];
+    for (int u = 0; u < 3; ++u) {
+        SplitHeff::Leg& L = S.leg[u];
+        L.terms = hb[u] != nullptr;
+        for (int p = 0; p < np; ++p)
+            if (pairs[p].a == u) L.terms = true;
+        L.on = L.terms;
+        for (int p = 0; p < np; ++p)
+            if (pairs[p].b == u) L.on = true;
+        if (!L.on) continue;
+        L.d = d[u];
+        if (u == 0) {
+            L.Pn = d[1] * d[2];
+        } else if (u == 1) {
+            L.Pn = d[0];
+            L.nb = d[2];
+        } else {
+            L.Pn = d[0] * d[1];
+        }
+        // tile efficiency: the operator side needs at least 16 rows and the
+        // stacked side at least 64 rows (else the FP64 kernel is as fast)
+        if (L.d < 16 || (long long)L.Pn * L.nb < 64) return false;
+        L.Pp = (int)((L.Pn + SPLIT_BM - 1) / SPLIT_BM * SPLIT_BM);
+        L.rows = (long long)L.Pp * L.nb;
+        L.Kc = L.d;   // slot 0: X
+        L.Qrows = (2 * L.d + SPLIT_BN - 1) / SPLIT_BN * SPLIT_BN;
+    }
+    if (!S.leg[0].on && !S.leg[1].on && !S.leg[2].on) return false;
+    S.np = np;
+    for (int p = 0; p < np; ++p) {
+        SplitHeff::PairPlan& P = S.pp[p];
+        P.a = pairs[p].a;
+        P.b = pairs[p].b;
+        P.r = pairs[p].r;
+        P.base = S.leg[P.a].Kc;
+        S.leg[P.a].Kc += S.leg[P.a].d * P.r;
+        P.Kz = (2 * d[P.b] + SPLIT_BK - 1) / SPLIT_BK * SPLIT_BK;
+        P.Qrows = S.leg[P.b].Qrows;
+    }
+    for (int u = 0; u < 3; ++u) {
+        SplitHeff::Leg& L = S.leg[u];
+        if (!L.on) continue;
+        L.Kp = (2 * L.Kc + SPLIT_BK - 1) / SPLIT_BK * SPLIT_BK;
+        const size_t pe = (size_t)L.rows * L.Kp, qe = (size_t)L.Qrows * L.Kp;
+        grow_zeroed(c, c->shP[u], c->shP_cap[u], 2 * pe * sizeof(float));
+        grow_zeroed(c, c->shQ[u], c->shQ_cap[u], 2 * qe * sizeof(float));
+        L.Ph = c->shP[u];
+        L.Pl = L.Ph + pe;
+        L.Qh = c->shQ[u];
+        L.Ql = L.Qh + qe;
+    }
+    for (int p = 0; p < np; ++p) {
+        SplitHeff::PairPlan& P = S.pp[p];
+        const size_t ge = (size_t)P.r * P.Qrows * P.Kz;
+        grow_zeroed(c, c->shG[p], c->shG_cap[p], 2 * ge * sizeof(float));
+        P.Gh = c->shG[p];
+        P.Gl = P.Gh + ge;
+    }
+    // operator stacks Q_u = [H_block(u) | n stacks of the pairs with a = u]
+    auto pack_ops = [&](SplitHeff::Leg& L, const cplx* src, int nmat, long long k_off_c, int Kc_write) {
+        SplitPackArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.src = src;
+        a.R = src ? L.d : 0;
+        a.Ki = L.d;
+        a.Ko = std::max(1, nmat);
+        a.s_r = 1;
+        a.s_ki = L.d;
+        a.s_ko = (long long)L.d * L.d;
+        a.Bi = a.Bo = 1;
+        a.embed = 1;
+        a.Rpad = L.Qrows / 2;
+        a.Kc = Kc_write;
+        a.pitch = L.Kp;
+        a.k_off = 2 * k_off_c;
+        a.hi = L.Qh;
+        a.lo = L.Ql;
+        c->stats[3] += split_pack(a, c->stream);
+    };
+    for (int u = 0; u < 3; ++u) {
+        SplitHeff::Leg& L = S.leg[u];
+        if (!L.on) continue;
+        if (hb[u]) pack_ops(L, hb[u], 1, 0, L.d);
+        else pack_ops(L, nullptr, 1, 0, L.d);   // no block term: zero slot
+        for (int p = 0; p < np; ++p)
+            if (S.pp[p].a == u) pack_ops(L, pairs[p].Na, S.pp[p].r, S.pp[p].base, L.d * S.pp[p].r);
+        if (L.Kp > 2 * L.Kc) pack_ops(L, nullptr, 1, L.Kc, (L.Kp - 2 * L.Kc) / 2);   // K padding
+    }
+    // G stacks: the operator side of Z_i = G_i x_b X, one padded block per i
+    for (int p = 0; p < np; ++p) {
+        SplitHeff::PairPlan& P = S.pp[p];
+        SplitPackArgs a;
+        std::memset(&a, 0, sizeof(a));
+        const int db = d[P.b];
+        a.src = pairs[p].G;
+        a.R = db;
+        a.Ki = db;
+        a.Ko = 1;
+        a.s_r = 1;
+        a.s_ki = db;
+        a.Bi = P.r;
+        a.s_bi = (long long)db * db;
+        a.Bo = 1;
+        a.embed = 1;
+        a.Rpad = P.Qrows / 2;
+        a.Kc = P.Kz / 2;
+        a.rb_i = P.Qrows;
+        a.pitch = P.Kz;
+        a.hi = P.Gh;
+        a.lo = P.Gl;
+        c->stats[3] += split_pack(a, c->stream);
+    }
+    S.ok = true;
+    return true;
+}
+
+int* split_flag(ttn_ctx* c) {
+    if (c->split_cap < 256) grow_split_ws(c, 256);
+    return reinterpret_cast<int*>(c->split_ws);
+}
+
+// y = H_eff x with the prepared stacks.
+void split_heff_apply(ttn_ctx* c, const SplitHeff& S, const cplx* x, cplx* y) {
+    const int d0 = S.d[0], d1 = S.d[1], d2 = S.d[2];
+    int* flag = split_flag(c);
+    // 1. X into slot 0 of every stacked operand
+    for (int u = 0; u < 3; ++u) {
+        const SplitHeff::Leg& L = S.leg[u];
+        if (!L.on) continue;
+        SplitPackArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.src = x;
+        a.Ko = 1;
+        a.Bi = a.Bo = 1;
+        if (u == 0) {
+            a.R = d1 * d2; a.s_r = d0; a.Ki = d0; a.s_ki = 1;
+        } else if (u == 1) {
+            a.R = d0; a.s_r = 1; a.Ki = d1; a.s_ki = d0; a.Bi = d2; a.s_bi = (long long)d0 * d1; a.rb_i = L.Pp;
+        } else {
+            a.R = d0 * d1; a.s_r = 1; a.Ki = d2; a.s_ki = (long long)d0 * d1;
+        }
+        a.Rpad = a.R;
+        a.Kc = L.d;
+        a.pitch = L.Kp;
+        a.hi = L.Ph;
+        a.lo = L.Pl;
+        ProfScope ps(c, PK_PACK, 0.0, (double)a.R * a.Bi * L.d * 32.0);
+        c->stats[3] += split_pack(a, c->stream);
+    }
+    // 2. channel intermediates Z_i = G_i x_b X, written into the K slots of P_a
+    const int BIG = 1 << 30;
+    for (int p = 0; p < S.np; ++p) {
+        const SplitHeff::PairPlan& P = S.pp[p];
+        const SplitHeff::Leg& Lb = S.leg[P.b];
+        const SplitHeff::Leg& La = S.leg[P.a];
+        const long long K2 = La.Kp / 2;
+        SplitMma m;
+        std::memset(&m, 0, sizeof(m));
+        m.Ph = Lb.Ph; m.Pl = Lb.Pl; m.P_rows = Lb.rows; m.P_pitch = Lb.Kp;
+        m.Qh = P.Gh; m.Ql = P.Gl; m.Q_rows = (long long)P.r * P.Qrows; m.Q_pitch = P.Kz;
+        m.Kp = P.Kz;
+        m.Pn = Lb.Pn; m.Pp = Lb.Pp;
+        m.Qn = Lb.d; m.Qp = P.Qrows;
+        m.alpha = C(1.0);
+        m.beta = C(0.0);
+        m.max_split = 1;
+        if (P.b == 1) {
+            m.Bi = d2; m.Bo = P.r; m.p_sbi = Lb.Pp; m.q_sbo = P.Qrows;
+        } else {
+            m.Bi = P.r; m.Bo = 1; m.q_sbi = P.Qrows;
+        }
+        SplitOut o;
+        std::memset(&o, 0, sizeof(o));
+        o.hi = La.Ph + 2 * P.base;
+        o.lo = La.Pl + 2 * P.base;
+        o.pd = BIG;
+        o.qd = BIG;
+        const int a = P.a, b = P.b;
+        if (a == 0 && b == 1) {
+            o.sp1 = 1; o.sq1 = K2; o.sbi = (long long)d1 * K2; o.sbo = d0;
+        } else if (a == 0 && b == 2) {
+            o.pd = d0; o.sp1 = 1; o.sp2 = K2; o.sq1 = (long long)d1 * K2; o.sbi = d0;
+        } else if (a == 1 && b == 0) {
+            o.pd = d1; o.sp1 = 1; o.sp2 = (long long)La.Pp * K2; o.sq1 = K2; o.sbi = d1;
+        } else if (a == 1 && b == 2) {
+            o.pd = d0; o.sp1 = K2; o.sp2 = 1; o.sq1 = (long long)La.Pp * K2; o.sbi = d1;
+        } else if (a == 2 && b == 0) {
+            o.pd = d1; o.sp1 = (long long)d0 * K2; o.sp2 = 1; o.sq1 = K2; o.sbi = d2;
+        } else {   // a == 2, b == 1
+            o.sp1 = K2; o.sq1 = (long long)d0 * K2; o.sbi = 1; o.sbo = d2;
+        }
+        m.out = &o;
+        const double fl = 8.0 * Lb.Pn * (double)Lb.d * Lb.d * (P.b == 1 ? (double)d2 * P.r : (double)P.r);
+        ProfScope ps(c, PK_TC, fl, 0.0);
+        ps.shape[0] = Lb.Pn; ps.shape[1] = Lb.d; ps.shape[2] = Lb.d; ps.shape[3] = m.Bi * m.Bo;
+        int n = split_mma(m, flag, nullptr, 0, c->stream);
+        if (n < 0) throw TtnError(TTN_ERR_CUDA, "split channel contraction launch failed");
+        c->stats[3] += n;
+    }
+    // 3. one long-K contraction per leg: Y (+)= Q_u x_u P_u
+    bool first = true;
+    for (int u = 0; u < 3; ++u) {
+        const SplitHeff::Leg& L = S.leg[u];
+        if (!L.terms) continue;
+        SplitMma m;
+        std::memset(&m, 0, sizeof(m));
+        m.Ph = L.Ph; m.Pl = L.Pl; m.P_rows = L.rows; m.P_pitch = L.Kp;
+        m.Qh = L.Qh; m.Ql = L.Ql; m.Q_rows = L.Qrows; m.Q_pitch = L.Kp;
+        m.Kp = L.Kp;
+        m.Pn = L.Pn; m.Pp = L.Pp;
+        m.Qn = L.d; m.Qp = L.Qrows;
+        m.Bi = L.nb; m.Bo = 1;
+        m.p_sbi = u == 1 ? L.Pp : 0;
+        m.C = y;
+        if (u == 0) {
+            m.c_p = d0; m.c_q = 1;
+        } else if (u == 1) {
+            m.c_p = 1; m.c_q = d0; m.c_bi = (long long)d0 * d1;
+        } else {
+            m.c_p = 1; m.c_q = (long long)d0 * d1;
+        }
+        m.alpha = C(1.0);
+        m.beta = C(first ? 0.0 : 1.0);
+        m.max_split = SPLIT_K_MAX;
+        const size_t pb = split_mma_partials(m);
+        if (c->split_cap < 256 + pb) grow_split_ws(c, 256 + pb);
+        flag = reinterpret_cast<int*>(c->split_ws);
+        const double fl = 8.0 * (double)L.Pn * L.nb * L.d * L.Kc;
+        ProfScope ps(c, PK_TC, fl, 0.0);
+        ps.shape[0] = L.Pn; ps.shape[1] = L.d; ps.shape[2] = L.Kc; ps.shape[3] = L.nb;
+        int n = split_mma(m, flag, reinterpret_cast<uint8_t*>(c->split_ws) + 256, c->split_cap - 256, c->stream);
+        if (n < 0) throw TtnError(TTN_ERR_CUDA, "split stacked contraction launch failed");
+        c->stats[3] += n;
+        first = false;
+    }
+    if (first) c->stats[3] += k_fill(y, (long long)d0 * d1 * d2, C(0.0), c->stream);
+}
+
 void assemble(ttn_ctx* c, const Env& e, cplx* out) {
     c->stats[3] += k_assemble_block(out, e.has_H ? e.H : nullptr, e.D, e.nops, (int)e.sites.size(),
                                     e.d_sites, e.dops, (int)e.driven.size(), e.d_driven, c->d_coef, c->stream);
@@ -492,6 +821,7 @@ template <class F>
 void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
     cudaStream_t s = c->stream;
     const double tol = (c->prec == TTN_FP64) ? 1e-13 : 1e-9;
+    const int mmax = test_krylov_mmax();
     cplx* V = c->Kbasis;
     const long long ld = n;
     c->stats[3] += k_norm2_partial(x, n, c->kpn, s);
@@ -509,9 +839,13 @@ void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
         c->stats[3] += k_orth_update_ex(V, ld, j + 1, part2, w, n, 2, nullptr, c->kpn, c->kh2, 0, -1, s);
         c->stats[3] += k_krylov_scalars_ex(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
         CUDA_OK(cudaMemcpyAsync(c->hflag, &c->ks->converged, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        c->hflag[2] = 0;
+        if (c->split_ws)   // a tensor-core wait that gave up leaves garbage: report it first
+            CUDA_OK(cudaMemcpyAsync(c->hflag + 2, c->split_ws, sizeof(int), cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
+        if (c->hflag[2]) check_split_flag(c);
         if (c->hflag[1]) throw TtnError(TTN_ERR_NUMERIC, "non-finite value in Lanczos");
-        if (c->hflag[0] || j == KRYLOV_MMAX - 1) break;
+        if (c->hflag[0] || j == mmax - 1) break;
         c->stats[3] += k_scale_copy_dev(w, n, &c->ks->inv_scale, w, s);
     }
     if (!c->hflag[0]) {
@@ -696,7 +1030,12 @@ void node_evolve(ttn_ctx* c, int k, double tau) {
     }
     Pair pairs[3];
     int np = setup_pairs(c, e, pairs);
-    krylov(c, c->T[k], nd.s, 0.0, -tau, [&](const cplx* x, cplx* y) { heff_apply(c, nd.d, hbs, Dl, pairs, np, x, y); });
+    SplitHeff S;
+    const bool sp = split_heff_prepare(c, S, nd.d, hbs, pairs, np);
+    krylov(c, c->T[k], nd.s, 0.0, -tau, [&](const cplx* x, cplx* y) {
+        if (sp) split_heff_apply(c, S, x, y);
+        else heff_apply(c, nd.d, hbs, Dl, pairs, np, x, y);
+    });
 }
 
 // R <- exp(+i tau H_link) R, rows in basis of er, columns of ec
@@ -712,8 +1051,12 @@ void link_evolve(ttn_ctx* c, const Env& er, const Env& ec, double tau) {
         }
     Pair pairs[3];
     int np = setup_pairs(c, e, pairs);
-    krylov(c, c->Rbuf, (long long)d[0] * d[1], 0.0, tau,
-           [&](const cplx* x, cplx* y) { heff_apply(c, d, hbs, Dl, pairs, np, x, y); });
+    SplitHeff S;
+    const bool sp = split_heff_prepare(c, S, d, hbs, pairs, np);
+    krylov(c, c->Rbuf, (long long)d[0] * d[1], 0.0, tau, [&](const cplx* x, cplx* y) {
+        if (sp) split_heff_apply(c, S, x, y);
+        else heff_apply(c, d, hbs, Dl, pairs, np, x, y);
+    });
 }
 
 std::vector<std::pair<int, int>> node_children(const ttn_ctx* c, int k) {
@@ -1310,6 +1653,11 @@ void ttn_destroy(ttn_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (void* p : c->allocs) cudaFree(p);
     if (c->split_ws) cudaFree(c->split_ws);
+    for (int i = 0; i < 3; ++i) {
+        if (c->shP[i]) cudaFree(c->shP[i]);
+        if (c->shQ[i]) cudaFree(c->shQ[i]);
+        if (c->shG[i]) cudaFree(c->shG[i]);
+    }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->hflag) cudaFreeHost(c->hflag);
     delete c;
@@ -1670,7 +2018,9 @@ ttn_status ttn_apply_heff(ttn_ctx* c, int k, const double* x, double* y) {
             }
         Pair pairs[3];
         int np = setup_pairs(c, e, pairs);
-        heff_apply(c, nd.d, hbs, Dl, pairs, np, c->tmp[1], c->tmp[2]);
+        SplitHeff S;
+        if (split_heff_prepare(c, S, nd.d, hbs, pairs, np)) split_heff_apply(c, S, c->tmp[1], c->tmp[2]);
+        else heff_apply(c, nd.d, hbs, Dl, pairs, np, c->tmp[1], c->tmp[2]);
         CUDA_OK(cudaMemcpyAsync(y, c->tmp[2], sizeof(cplx) * nd.s, cudaMemcpyDeviceToHost, c->stream));
         sync_check(c);
     });
@@ -1813,6 +2163,112 @@ ttn_status ttn_selftest_qr(const double* A, int M, int D, const int* cand, int n
         if (n_dependent) *n_dependent = ndep;
         if (ms) *ms = t;
     });
+}
+
+ttn_status ttn_selftest_contract_host(const double* A, const double* B, double* Cout, int M, int N, int K,
+                                      int precision, int* path, float* ms) {
+    if (!A || !B || !Cout || M < 1 || N < 1 || K < 1 || (long long)M * N > (1LL << 26) ||
+        (long long)M * K > (1LL << 26) || (long long)K * N > (1LL << 26) ||
+        (precision != TTN_FP64 && precision != TTN_SPLIT_TF32X3))
+        return TTN_ERR_ARG;
+    ttn_ctx tmp;
+    tmp.prec = (ttn_precision)precision;
+    return guard(&tmp, [&] {
+        struct Free {
+            ttn_ctx* t;
+            ~Free() {
+                for (void* p : t->allocs) cudaFree(p);
+                t->allocs.clear();
+                if (t->split_ws) cudaFree(t->split_ws);
+                t->split_ws = nullptr;
+            }
+        } fr{&tmp};
+        cplx* dA = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)M * K);
+        cplx* dB = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)K * N);
+        cplx* dC = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)M * N);
+        CUDA_OK(cudaMemcpy(dA, A, sizeof(cplx) * (size_t)M * K, cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(dB, B, sizeof(cplx) * (size_t)K * N, cudaMemcpyHostToDevice));
+        GemmArgs g = base_args();
+        g.M = M; g.N = N; g.Ki = K;
+        g.A = dA; g.a_m = 1; g.a_ki = M;
+        g.B = dB; g.b_ki = 1; g.b_n = K;
+        g.C = dC; g.c_m = 1; g.c_n = M;
+        const bool tc = precision == TTN_SPLIT_TF32X3 && split_workspace_bytes(g) > 0;
+        if (tc) grow_split_ws(&tmp, split_workspace_bytes(g));   // outside the timed region
+        cudaEvent_t e0, e1;
+        CUDA_OK(cudaEventCreate(&e0));
+        CUDA_OK(cudaEventCreate(&e1));
+        CUDA_OK(cudaEventRecord(e0, nullptr));
+        gemm(&tmp, g);
+        CUDA_OK(cudaEventRecord(e1, nullptr));
+        CUDA_OK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CUDA_OK(cudaGetLastError());
+        check_split_flag(&tmp);
+        CUDA_OK(cudaMemcpy(Cout, dC, sizeof(cplx) * (size_t)M * N, cudaMemcpyDeviceToHost));
+        if (path) *path = tc ? 1 : 0;
+        if (ms) *ms = t;
+    });
+}
+
+ttn_status ttn_selftest_fp64_peak(int method, double* tflops) {
+    if (!tflops || (method != 0 && method != 1)) return TTN_ERR_ARG;
+    ttn_ctx tmp;
+    return guard(&tmp, [&] {
+        struct Free {
+            ttn_ctx* t;
+            ~Free() {
+                for (void* p : t->allocs) cudaFree(p);
+                t->allocs.clear();
+            }
+        } fr{&tmp};
+        double* out = (double*)dalloc(&tmp, 64);
+        int dev = 0, nsm = 0;
+        CUDA_OK(cudaGetDevice(&dev));
+        CUDA_OK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int blocks = 8 * nsm;   // 2048 threads per SM: every FP64 unit busy
+        cudaEvent_t e0, e1;
+        CUDA_OK(cudaEventCreate(&e0));
+        CUDA_OK(cudaEventCreate(&e1));
+        k_fp64_probe(method, blocks, 64, out, nullptr);   // warm-up
+        int iters = 256;
+        float t = 0.f;
+        double fl = 0.0;
+        for (int rep = 0; rep < 12; ++rep) {   // grow until a launch takes >= 20 ms
+            CUDA_OK(cudaEventRecord(e0, nullptr));
+            fl = k_fp64_probe(method, blocks, iters, out, nullptr);
+            CUDA_OK(cudaEventRecord(e1, nullptr));
+            CUDA_OK(cudaEventSynchronize(e1));
+            CUDA_OK(cudaGetLastError());
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t >= 20.f) break;
+            iters *= 2;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *tflops = fl / (t * 1e-3) / 1e12;
+    });
+}
+
+ttn_status ttn_test_inject(int kind, long long value) {
+    if (value < 0) return TTN_ERR_ARG;
+    switch (kind) {
+        case TTN_INJECT_NONE:
+            g_inj_tc_stall = 0;
+            g_inj_mmax = 0;
+            g_inj_alloc_fail = 0;
+            return TTN_OK;
+        case TTN_INJECT_TC_STALL: g_inj_tc_stall = value; return TTN_OK;
+        case TTN_INJECT_KRYLOV_MMAX:
+            if (value > KRYLOV_MMAX) return TTN_ERR_ARG;
+            g_inj_mmax = (int)value;
+            return TTN_OK;
+        case TTN_INJECT_ALLOC_FAIL: g_inj_alloc_fail = value; return TTN_OK;
+        default: return TTN_ERR_ARG;
+    }
 }
 
 ttn_status ttn_profile_records(const ttn_ctx* c, double* out, int max_records, int* n_records) {

@@ -60,7 +60,14 @@ SIGNATURES = [
     ("ttn_profile_records", ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
     ("ttn_reset_stats", ctypes.c_int, [_P]),
     ("ttn_contract_split_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    ("ttn_selftest_contract_host", ctypes.c_int, [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, _I, ctypes.POINTER(ctypes.c_float)]),
+    ("ttn_selftest_fp64_peak", ctypes.c_int, [ctypes.c_int, _D]),
+    ("ttn_test_inject", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong]),
 ]
+
+# fault-injection hooks of ttn_test_inject
+INJECT_NONE, INJECT_TC_STALL, INJECT_KRYLOV_MMAX, INJECT_ALLOC_FAIL = 0, 1, 2, 3
 
 _lib = None
 
@@ -112,6 +119,44 @@ def selftest_qr(A, cand=None):
     if st != 0:
         raise TTNError(st, "selftest_qr(%d, %d)" % (M, D))
     return Q, R, nd.value, ms.value
+
+
+def contract_host(A, B, precision):
+    """C = A B of host complex matrices on the device (FP64 kernel, or the
+    split-precision tensor-core path when the shape fills its tiles): returns
+    (C, tensor_core_path_ran, device ms)."""
+    lib = load()
+    A = np.asfortranarray(np.asarray(A, dtype=np.complex128))
+    B = np.asfortranarray(np.asarray(B, dtype=np.complex128))
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.zeros((M, N), dtype=np.complex128, order="F")
+    path = ctypes.c_int(0)
+    ms = ctypes.c_float(0.0)
+    st = lib.ttn_selftest_contract_host(A.ctypes.data_as(_D), B.ctypes.data_as(_D), C.ctypes.data_as(_D),
+                                        M, N, K, int(precision), ctypes.byref(path), ctypes.byref(ms))
+    if st != 0:
+        raise TTNError(st, "selftest_contract_host(%d, %d, %d)" % (M, N, K))
+    return C, bool(path.value), ms.value
+
+
+def fp64_peak(method=0):
+    """Measured FP64 rate in TFLOP/s: method 0 FMA chains (DFMA), 1 FP64
+    tensor-core mma.sync m8n8k4 (DMMA)."""
+    lib = load()
+    out = np.zeros(1)
+    st = lib.ttn_selftest_fp64_peak(int(method), _dptr(out))
+    if st != 0:
+        raise TTNError(st, "selftest_fp64_peak(%d)" % method)
+    return float(out[0])
+
+
+def inject(kind, value=0):
+    """Set a fault-injection hook (INJECT_*); INJECT_NONE clears all."""
+    st = load().ttn_test_inject(int(kind), int(value))
+    if st != 0:
+        raise TTNError(st, "test_inject(%d, %d)" % (kind, value))
 
 
 def contract_split_noalloc(A_ptr, B_ptr, C_ptr, M, N, K, stream=None):

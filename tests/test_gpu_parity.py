@@ -266,3 +266,117 @@ def test_full_size_8x8_chi128_no_interaction_closed_form(native):
     tgt.set_product_state(states)
     assert abs(g.fidelity(tgt) - 1) < 1e-11
     g.close()
+
+
+# ---------------------------------------------------------------------------
+# H_eff at the benchmark size, interacting, against the oracle element by
+# element: 8x8 lattice, chi = 128, C6/a^6 = 20 with all 2016 pairs, three
+# driven atoms.  A level-4 node (128, 128, 128) runs the 64-wide FP64 tiles and
+# the r = 16 / 32 channel sums; a level-2 node (81, 81, 128) the 32-wide tiles
+# (81 -> 96 padding).  The oracle keeps drive operators only for the driven
+# atoms (the others' coefficients are zero), which keeps its environment
+# build to seconds.
+FULL_DRIVE = [0, 27, 50]
+
+
+@pytest.fixture(scope="module")
+def full_size_heff_ref():
+    Lx = Ly = 8
+    chi = 128
+    xy = W.square_lattice(Lx, Ly)
+    sched = W.random_constant_schedule(64, 31, atoms=FULL_DRIVE)
+    o = ottn.OracleTTN(Lx, Ly, chi, xy, 20.0, drive_atoms=FULL_DRIVE)
+    o.set_schedule(sched)
+    tr = o.tree
+    Ts = W.random_ttn_tensors([tr.shape(k) for k in range(tr.n_nodes)], 41)
+    o.set_tensors(Ts)
+    saved_T = [x.copy() for x in o.T]
+    rng = np.random.default_rng(17)
+    cases = []
+    for k in (tr.level_nodes[4][0], tr.level_nodes[2][-1]):
+        o.T = [x.copy() for x in saved_T]
+        shape = tr.shape(k)
+        X = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+        _oracle_centre_to(o, k)
+        Hb, ch = o.heff_setup(k, o.coef(0.0))
+        cases.append((k, X, o.heff_apply(X, Hb, ch)))
+    return xy, sched, Ts, cases
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("split", 6e-6)])
+def test_heff_full_size_8x8_chi128_vs_oracle(native, full_size_heff_ref, prec, tol):
+    xy, sched, Ts, cases = full_size_heff_ref
+    g = native.TTN(8, 8, 128)
+    g.set_precision(native.FP64 if prec == "fp64" else native.SPLIT_TF32X3)
+    g.set_hamiltonian(xy, 20.0)
+    g.apply_pulse(sched)
+    for k, X, y_ref in cases:
+        assert g.node_info(k)[0] == y_ref.shape
+        for n, T in enumerate(Ts):
+            g.set_node(n, T)
+        g.refresh_envs()
+        y = g.apply_heff(k, X)
+        err = np.max(abs(y - y_ref)) / np.max(abs(y_ref))
+        assert err <= tol, (k, err)
+        if prec == "split":
+            assert err > 0.0        # the tensor-core path ran
+    g.close()
+
+
+# ---------------------------------------------------------------------------
+# Config-2 trajectories (4x4, chi = 64, FP64) against stored oracle values:
+# the GHZ circuit scheduled serially and with r_G = sqrt(8) a, from its first
+# CZ layer, 24 steps of dt = 0.05 from a seeded random product state.  The
+# expected values were written by tests/golden/make_cfg2_trajectories.py,
+# which runs only the CPU oracle.  Bound: |1 - F_gpu / F_ref| <= 1e-10 for
+# the return probability F = |<psi(0)|psi(t)>|^2 (of order one), 1e-10 on the
+# overlaps with psi(0) and with the 16-atom GHZ target and on the
+# populations, 1e-9 on the energy.
+def _load_cfg2():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cfg2_trajectories.txt")
+    out, cur = {}, None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, *vals = line.split()
+        if key == "schedule":
+            cur = out.setdefault(vals[0], {})
+        else:
+            cur[key] = np.array([float(v) for v in vals])
+    return out
+
+
+@pytest.mark.parametrize("name", ["serial", "greedy"])
+def test_cfg2_trajectory_vs_oracle(native, name):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_cfg2", os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_cfg2_trajectories.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    ref = _load_cfg2()[name]
+    xy, sched = mk.cfg2_schedule(dict(mk.SCHEDULES)[name])
+    g = native.TTN(mk.LX, mk.LY, mk.CHI)
+    g.set_hamiltonian(xy, mk.C6)
+    g.apply_pulse(sched)
+    g.set_product_state(W.random_product_amps(mk.LX * mk.LY, mk.SEED))
+    for _ in range(mk.STEPS):
+        g.step(mk.DT)
+    start = native.TTN(mk.LX, mk.LY, 1)
+    start.set_product_state(W.random_product_amps(mk.LX * mk.LY, mk.SEED))
+    ret = g.overlap(start)
+    ret_ref = complex(*ref["return"])
+    F, F_ref = abs(ret) ** 2, abs(ret_ref) ** 2
+    assert F_ref > 1e-3
+    assert abs(1 - F / F_ref) <= 1e-10, (F, F_ref)
+    assert abs(ret - ret_ref) <= 1e-10
+    tgt = native.TTN(mk.LX, mk.LY, 2)
+    tgt.set_ghz([1] * (mk.LX * mk.LY), 0.0)
+    ov = g.overlap(tgt)
+    assert abs(ov - complex(*ref["overlap"])) <= 1e-10
+    assert abs(g.norm() - ref["norm"][0]) <= 1e-10
+    assert abs(g.energy() - ref["energy"][0]) <= 1e-9
+    for w in range(3):
+        assert np.max(abs(g.measure(w) - ref["measure%d" % w])) <= 1e-10, w
+    g.close()
+    tgt.close()
+    start.close()

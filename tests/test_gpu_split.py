@@ -32,9 +32,41 @@ NORM_TOL = 1e-8
                                    (128, 128, 16384), (81, 81, 10368), (100, 90, 5003)])
 @pytest.mark.parametrize("tf32_exact", [False, True])
 def test_split_contraction_vs_fp64_kernel(native, M, N, K, tf32_exact):
+    # the split path against the library's FP64 kernel on device-generated
+    # operands (the FP64 kernel itself is pinned to host products below)
     err = native.selftest_contract(M, N, K, native.SPLIT_TF32X3, seed=3, tf32_exact=tf32_exact)
     assert 0.0 < err < CONTRACT_TOL, err
-    assert native.selftest_contract(M, N, K, native.FP64, seed=3) == 0.0
+
+
+# Host reference: NumPy complex128 A @ B on the same seeded operands.  Shapes
+# of each kind the TDVP step runs: square, tall (the Q side of an absorb),
+# long K with split-K, 81-wide level-2 blocks, and ragged sizes.
+HOST_SHAPES = [(128, 128, 128), (16384, 128, 128), (128, 128, 16384), (81, 81, 10368), (200, 70, 33),
+               (100, 90, 5003), (81, 729, 81)]
+
+
+@pytest.mark.parametrize("M,N,K", HOST_SHAPES)
+def test_fp64_contraction_vs_host_product(native, M, N, K):
+    rng = np.random.default_rng(M + 7 * N + 13 * K)
+    A = rng.uniform(-1, 1, (M, K)) + 1j * rng.uniform(-1, 1, (M, K))
+    B = rng.uniform(-1, 1, (K, N)) + 1j * rng.uniform(-1, 1, (K, N))
+    ref = A @ B
+    C, tc, _ = native.contract_host(A, B, native.FP64)
+    assert not tc
+    # rounding of a K-term FP64 dot product in two summation orders
+    assert np.max(abs(C - ref)) <= 1e-13 * np.sqrt(K) * np.max(abs(ref))
+
+
+@pytest.mark.parametrize("M,N,K", HOST_SHAPES)
+def test_split_contraction_vs_host_product(native, M, N, K):
+    rng = np.random.default_rng(M + 7 * N + 13 * K)
+    A = rng.uniform(-1, 1, (M, K)) + 1j * rng.uniform(-1, 1, (M, K))
+    B = rng.uniform(-1, 1, (K, N)) + 1j * rng.uniform(-1, 1, (K, N))
+    ref = A @ B
+    C, tc, _ = native.contract_host(A, B, native.SPLIT_TF32X3)
+    assert tc                       # these shapes fill the tensor-core tiles
+    err = np.max(abs(C - ref)) / np.max(abs(ref))
+    assert 0.0 < err < CONTRACT_TOL, err
 
 
 @pytest.fixture(scope="module")
