@@ -220,6 +220,22 @@ ttn_status ttn_reset_stats(ttn_ctx* ctx);
 ttn_status ttn_selftest_contract_host(const double* A, const double* B, double* C, int M, int N, int K,
                                       int precision, int* path, float* ms);
 
+/* Truncated singular value decomposition of a bond matrix, no context needed
+ * (Sec. "Tensor network simulations": the bond dimension chi caps the kept
+ * singular values; discarding sigma_i < eps * sigma_max as well).
+ * A: host, M x N complex (interleaved, column-major, lda = M), M >= N,
+ * 1 <= N <= 256, M * N <= 2^26.  On the device: A = Q R (the gauge-move QR
+ * with its deterministic completion), a one-sided Jacobi SVD of R, U = Q U_R.
+ * Keeps k = min(chi, #{sigma_i >= eps sigma_max}) (at least 1) values in
+ * descending order: U (M x k), S (k doubles), Vh (k x N, column-major, the
+ * conjugate transpose of V's kept columns), so that A ~ U diag(S) Vh; the
+ * caller's buffers must hold min(chi, N) columns/values.  *k_out receives k,
+ * *discarded (may be NULL) the discarded weight sum_{i >= k} sigma_i^2 /
+ * sum_i sigma_i^2.  Bad sizes -> TTN_ERR_ARG; a grid-barrier wait that gave
+ * up -> TTN_ERR_TIMEOUT. */
+ttn_status ttn_svd_truncate(const double* A, int M, int N, int chi, double eps, double* U, double* S, double* Vh,
+                            int* k_out, double* discarded);
+
 /* FP64 throughput probe, no context needed: method 0 runs independent FP64
  * fused multiply-add chains on every SM (the FP64 ALU, DFMA), method 1 chains
  * of FP64 tensor-core instructions (mma.sync m8n8k4 f64, DMMA); *tflops

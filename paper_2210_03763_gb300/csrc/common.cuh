@@ -45,14 +45,14 @@ int split_pack(const SplitPackArgs& p, cudaStream_t stream);
 
 // Packed output of a split contraction: the epilogue writes TF32 hi/lo
 // planes (as split_pack with embed = 0) at float2 position
-// (p % pd)*sp1 + (p / pd)*sp2 + (q % qd)*sq1 + (q / qd)*sq2 + bi*sbi + bo*sbo
-// for output (P row p, Q row q, batch bi, bo); hi/lo already offset to the
-// first slot.
+// (p % pd)*sp1 + (p / pd)*sp2 + q*sq + bi*sbi + bo*sbo for output (P row p,
+// Q row q, batch bi, bo); hi/lo already offset to the first slot.  Writes
+// are coalesced when sp1 = 1 (consecutive P rows land next to each other).
 struct SplitOut {
     float* hi;
     float* lo;
-    int pd, qd;
-    long long sp1, sp2, sq1, sq2, sbi, sbo;
+    int pd;
+    long long sp1, sp2, sq, sbi, sbo;
 };
 
 // One split contraction on packed planes: C(p, q) = alpha sum_k P(p, k) Q(q, k)
@@ -73,6 +73,8 @@ struct SplitMma {
     long long p_sbi, p_sbo, q_sbi, q_sbo;   // real-row offsets of batch (bi, bo)
     cplx* C;
     long long c_p, c_q, c_bi, c_bo;
+    int c_pd;                    // > 0: P row offset (p % c_pd)*c_p + (p / c_pd)*c_p2
+    long long c_p2;
     cplx alpha, beta;
     const SplitOut* out;         // non-null: packed output (alpha = 1, beta = 0)
     int max_split;               // split-K cap (1: none; forced to 1 with `out`)
@@ -182,6 +184,20 @@ constexpr int QR_SC_MAXR = 64;   // structured completion when the kept rank r <
 // of the cooperative column loop gave up (A and R are then undefined).
 int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand,
             QrScratch& ws, cudaStream_t s, int* n_dependent_host);
+
+// ---- truncated SVD (svd.cu) -----------------------------------------------------
+// One-sided Jacobi SVD of the N x N column-major R (N <= 256) in place: R's
+// columns end mutually orthogonal, V (N x N) accumulates the rotations
+// (R_in V = R_out).  One cooperative launch; bar: 2 unsigned, err: set when a
+// grid-barrier wait gave up; info[0]: sweeps run.  Returns launches, -1 if
+// the cooperative launch failed.
+int svd_jacobi_square(cplx* R, cplx* V, int N, int max_sweeps, double tol, unsigned* bar, int* err, int* info,
+                      cudaStream_t s);
+// sigma_i = |r_i|, descending order, kept k = min(chi, #{sigma >= eps sigma_max})
+// (at least 1), discarded weight sum_{t >= k} sigma^2 / sum sigma^2;
+// Ur (N x k) = normalised kept columns, Vh (k x N) = their conj(V) rows.
+int svd_finish(const cplx* R, const cplx* V, int N, int chi, double eps, cplx* Ur, cplx* Vh, double* S, int* k,
+               double* disc, int* order, cudaStream_t s);
 
 // ---- test hooks (ttn_test_inject in ttn.cu) -----------------------------------
 // Stall time in ns for the next tensor-core launch (0: none; consumes one

@@ -277,6 +277,8 @@ constexpr int GEMM_THREADS = DRAIN_THREADS + 64;
 struct EpiArgs {
     cplx* C;
     long long c_p, c_q, c_bi, c_bo;   // output strides of P row p, Q row q, batch (bi, bo)
+    int c_pd;             // P row split: offset (p % c_pd)*c_p + (p / c_pd)*c_p2
+    long long c_p2;
     int Pn, Qn, Bi;       // valid complex rows of P and Q; inner batch extent
     long long p_sbi, p_sbo, q_sbi, q_sbo;   // real-row offset of batch (bi, bo) in P / Q (0: shared)
     int nkb;              // K' / BK
@@ -291,11 +293,11 @@ struct EpiArgs {
     unsigned long long stall_ns;   // test hook: > 0 makes the drain warps wait this long on a
                                    // barrier nothing arrives at, so the launch aborts as on a timeout
     // packed output (o_hi != nullptr): TF32 hi/lo planes at float2 position
-    // (p % pd)*sp1 + (p / pd)*sp2 + (q % qd)*sq1 + (q / qd)*sq2 + bi*sbi + bo*sbo
+    // (p % pd)*sp1 + (p / pd)*sp2 + q*sq + bi*sbi + bo*sbo
     float* o_hi;
     float* o_lo;
-    int o_pd, o_qd;
-    long long o_sp1, o_sp2, o_sq1, o_sq2, o_sbi, o_sbo;
+    int o_pd;
+    long long o_sp1, o_sp2, o_sq, o_sbi, o_sbo;
 };
 
 // Round a float to TF32 (10 mantissa bits, to nearest, ties to even) with
@@ -533,11 +535,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     // packed output: TF32 planes for a later contraction, no FP64
                     const long long pbase = (long long)(p % ea.o_pd) * ea.o_sp1 + (long long)(p / ea.o_pd) * ea.o_sp2 +
                                             bi * ea.o_sbi + bo * ea.o_sbo;
+                    const int q0 = (qt * BN + col0) >> 1;
 #pragma unroll
                     for (int j = 0; j < DCOLS; j += 2) {
-                        const int q = (qt * BN + col0 + j) >> 1;
+                        const int q = q0 + (j >> 1);
                         if (q >= ea.Qn) continue;
-                        const long long pos = pbase + (long long)(q % ea.o_qd) * ea.o_sq1 + (long long)(q / ea.o_qd) * ea.o_sq2;
+                        const long long pos = pbase + (long long)q * ea.o_sq;
                         float rh, rl, ih, il;
                         ff_to_tf32_pair(hi[j], lo[j], rh, rl);
                         ff_to_tf32_pair(hi[j + 1], lo[j + 1], ih, il);
@@ -546,7 +549,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     }
                     continue;
                 }
-                cplx* C = ea.C + bi * ea.c_bi + bo * ea.c_bo + p * ea.c_p;
+                cplx* C = ea.C + bi * ea.c_bi + bo * ea.c_bo + (long long)(p % ea.c_pd) * ea.c_p +
+                          (long long)(p / ea.c_pd) * ea.c_p2;
 #pragma unroll
                 for (int j = 0; j < DCOLS; j += 2) {
                     const int q = (qt * BN + col0 + j) >> 1;       // complex row of Q
@@ -601,7 +605,8 @@ __global__ void splitk_reduce_kernel(EpiArgs ea) {
             acc.y += w.y;
         }
         const int bi = b % ea.Bi, bo = b / ea.Bi;
-        cplx* cp = ea.C + bi * ea.c_bi + bo * ea.c_bo + p * ea.c_p + q * ea.c_q;
+        cplx* cp = ea.C + bi * ea.c_bi + bo * ea.c_bo + (long long)(p % ea.c_pd) * ea.c_p +
+                   (long long)(p / ea.c_pd) * ea.c_p2 + q * ea.c_q;
         cplx r;
         if (ea.mode == 0) {
             r = acc;
@@ -869,6 +874,8 @@ int split_mma(const SplitMma& m, int* err_flag, void* partials, size_t partial_b
     EpiArgs ea;
     std::memset(&ea, 0, sizeof(ea));
     ea.C = m.C; ea.c_p = m.c_p; ea.c_q = m.c_q; ea.c_bi = m.c_bi; ea.c_bo = m.c_bo;
+    ea.c_pd = m.c_pd > 0 ? m.c_pd : (1 << 30);
+    ea.c_p2 = m.c_p2;
     ea.Pn = m.Pn; ea.Qn = m.Qn; ea.Bi = m.Bi;
     ea.p_sbi = m.p_sbi; ea.p_sbo = m.p_sbo; ea.q_sbi = m.q_sbi; ea.q_sbo = m.q_sbo;
     ea.nkb = m.Kp / BK;
@@ -882,8 +889,8 @@ int split_mma(const SplitMma& m, int* err_flag, void* partials, size_t partial_b
     ea.stall_ns = test_take_tc_stall();
     if (m.out) {
         ea.o_hi = m.out->hi; ea.o_lo = m.out->lo;
-        ea.o_pd = m.out->pd; ea.o_qd = m.out->qd;
-        ea.o_sp1 = m.out->sp1; ea.o_sp2 = m.out->sp2; ea.o_sq1 = m.out->sq1; ea.o_sq2 = m.out->sq2;
+        ea.o_pd = m.out->pd;
+        ea.o_sp1 = m.out->sp1; ea.o_sp2 = m.out->sp2; ea.o_sq = m.out->sq;
         ea.o_sbi = m.out->sbi; ea.o_sbo = m.out->sbo;
     }
     // persistent: one CTA per SM walks the tiles, the smaller tile count

@@ -5,6 +5,7 @@
 // the same fixed order, so repeated runs are bitwise identical and every
 // block of a kernel sees the same reduced value.
 #include "common.cuh"
+#include <algorithm>
 #include <cmath>
 
 namespace {
@@ -555,6 +556,9 @@ int k_weighted_sum(const cplx* N, int nb, long long n, const double* W, int r, c
     if (n <= 0 || r <= 0) return 0;
     const size_t need = sizeof(double) * (size_t)nb * r;
     const int staged = need <= 48 * 1024;
-    weighted_sum_kernel<<<grid_for(n), 256, staged ? need : 0, s>>>(N, nb, n, W, r, G, staged);
+    // small blocks: the work per entry is nb * r FP64 FMAs, so spread the
+    // entries over every SM
+    const long long blocks = std::min<long long>((n + 63) / 64, 16 * 152);
+    weighted_sum_kernel<<<(unsigned)blocks, 64, staged ? need : 0, s>>>(N, nb, n, W, r, G, staged);
     return 1;
 }

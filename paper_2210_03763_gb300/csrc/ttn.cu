@@ -147,7 +147,7 @@ struct ttn_ctx {
 
     std::vector<Env> up, down, phys;
     Env dummy;
-    std::map<std::pair<const Env*, const Env*>, double*> vsub;   // G-stack weights
+    std::map<std::pair<const Env*, const Env*>, std::pair<double*, cplx*>> vsub;   // G-stack weights
 
     // kernel-level profile: event pairs around launches while enabled
     bool profiling = false;
@@ -168,6 +168,8 @@ struct ttn_ctx {
     size_t shQ_cap[3] = {0, 0, 0};
     float* shG[3] = {nullptr, nullptr, nullptr};
     size_t shG_cap[3] = {0, 0, 0};
+    float* shX[3] = {nullptr, nullptr, nullptr};
+    size_t shX_cap[3] = {0, 0, 0};
     int64_t stats[6] = {0, 0, 0, 0, 0, 0};
     double max_err = 0.0;
     std::vector<void*> allocs;
@@ -443,29 +445,49 @@ const Env& env_of(ttn_ctx* c, int k, int leg) {
     return ch >= 0 ? c->up[ch] : c->phys[-ch - 1];
 }
 
-double* vsub_for(ttn_ctx* c, const Env& a, const Env& b) {
+// Weights of the G stack: |S_b| x |S_a|, element (j, i) = V(a_i, b_j), as
+// real doubles (FP64 weighted sum) and as complex numbers (split contraction).
+std::pair<double*, cplx*> vsub_for(ttn_ctx* c, const Env& a, const Env& b) {
     auto key = std::make_pair(&a, &b);
     auto it = c->vsub.find(key);
     if (it != c->vsub.end()) return it->second;
-    // weights of the G stack: |S_b| x |S_a|, element (j, i) = V(a_i, b_j)
     size_t nb = b.sites.size(), na = a.sites.size();
     std::vector<double> h(nb * na);
+    std::vector<cplx> hc(nb * na);
     for (size_t i = 0; i < na; ++i)
-        for (size_t j = 0; j < nb; ++j) h[j + nb * i] = c->V[(size_t)a.sites[i] * c->N + b.sites[j]];
+        for (size_t j = 0; j < nb; ++j) {
+            h[j + nb * i] = c->V[(size_t)a.sites[i] * c->N + b.sites[j]];
+            hc[j + nb * i] = C(h[j + nb * i]);
+        }
     double* d = (double*)dalloc(c, sizeof(double) * std::max<size_t>(1, h.size()));
-    if (!h.empty()) CUDA_OK(cudaMemcpy(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
-    c->vsub[key] = d;
-    return d;
+    cplx* dc = (cplx*)dalloc(c, sizeof(cplx) * std::max<size_t>(1, h.size()));
+    if (!h.empty()) {
+        CUDA_OK(cudaMemcpy(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(dc, hc.data(), sizeof(cplx) * hc.size(), cudaMemcpyHostToDevice));
+    }
+    c->vsub[key] = {d, dc};
+    return c->vsub[key];
 }
 
-// G_i = sum_j V_ij n_j^(b) for every atom i of env a, into Gbuf (a weighted
-// sum of the n stack: memory and FP64 bound, no contraction needed)
+// G_i = sum_j V_ij n_j^(b) for every atom i of env a, into Gbuf: in split
+// precision a tensor-core contraction of the n stack with the weights when it
+// fills the tiles, else an FP64 weighted sum of the n stack.
 void build_G(ttn_ctx* c, const Env& a, const Env& b, cplx* G) {
     int r = (int)a.sites.size(), nbs = (int)b.sites.size();
     long long DD = (long long)b.D * b.D;
+    auto w = vsub_for(c, a, b);
+    GemmArgs g = base_args();
+    g.M = (int)DD; g.N = r; g.Ki = nbs;
+    g.A = b.nops; g.a_m = 1; g.a_ki = DD;
+    g.B = w.second; g.b_ki = 1; g.b_n = nbs;
+    g.C = G; g.c_m = 1; g.c_n = DD;
+    if (c->prec == TTN_SPLIT_TF32X3 && !g_force_fp64 && split_workspace_bytes(g) > 0) {
+        gemm(c, g);
+        return;
+    }
     ProfScope ps(c, PK_F64, 4.0 * r * (double)nbs * DD, 0.0);
     ps.shape[0] = (int)DD; ps.shape[1] = r; ps.shape[2] = nbs; ps.shape[3] = 1;
-    c->stats[3] += k_weighted_sum(b.nops, nbs, DD, vsub_for(c, a, b), r, G, c->stream);
+    c->stats[3] += k_weighted_sum(b.nops, nbs, DD, w.first, r, G, c->stream);
 }
 
 // Pairs of an effective Hamiltonian over envs e[0..2]; G stacks built.
@@ -560,6 +582,11 @@ struct SplitHeff {
         int Kz;               // K' of the G contraction (floats)
         int Qrows;            // padded real rows of one G matrix
         float *Gh = nullptr, *Gl = nullptr;
+        // transposed pairs (a later than b, except (1, 0)): X packed with
+        // leg a's index fastest, so the epilogue's stores are coalesced
+        bool trans = false;
+        int Xrows = 0, XPp = 0;
+        float *Xh = nullptr, *Xl = nullptr;
     } pp[3];
     int np = 0;
     int d[3] = {0, 0, 0};
@@ -607,6 +634,11 @@ bool split_heff_prepare(ttn_ctx* c, SplitHeff& S, const int* d, cplx* const* hb,
         S.leg[P.a].Kc += S.leg[P.a].d * P.r;
         P.Kz = (2 * d[P.b] + SPLIT_BK - 1) / SPLIT_BK * SPLIT_BK;
         P.Qrows = S.leg[P.b].Qrows;
+        P.trans = (P.a == 2 && P.b == 0) || (P.a == 2 && P.b == 1) || (P.a == 1 && P.b == 2);
+        if (P.trans) {
+            P.Xrows = P.b == 0 ? d[1] * d[2] : P.b == 1 ? d[0] * d[2] : d[0] * d[1];
+            P.XPp = (P.Xrows + SPLIT_BM - 1) / SPLIT_BM * SPLIT_BM;
+        }
     }
     for (int u = 0; u < 3; ++u) {
         SplitHeff::Leg& L = S.leg[u];
@@ -626,6 +658,12 @@ bool split_heff_prepare(ttn_ctx* c, SplitHeff& S, const int* d, cplx* const* hb,
         grow_zeroed(c, c->shG[p], c->shG_cap[p], 2 * ge * sizeof(float));
         P.Gh = c->shG[p];
         P.Gl = P.Gh + ge;
+        if (P.trans) {
+            const size_t xe = (size_t)P.XPp * P.Kz;
+            grow_zeroed(c, c->shX[p], c->shX_cap[p], 2 * xe * sizeof(float));
+            P.Xh = c->shX[p];
+            P.Xl = P.Xh + xe;
+        }
     }
     // operator stacks Q_u = [H_block(u) | n stacks of the pairs with a = u]
     auto pack_ops = [&](SplitHeff::Leg& L, const cplx* src, int nmat, long long k_off_c, int Kc_write) {
@@ -725,45 +763,75 @@ void split_heff_apply(ttn_ctx* c, const SplitHeff& S, const cplx* x, cplx* y) {
         const SplitHeff::Leg& Lb = S.leg[P.b];
         const SplitHeff::Leg& La = S.leg[P.a];
         const long long K2 = La.Kp / 2;
+        const int a = P.a, b = P.b;
         SplitMma m;
         std::memset(&m, 0, sizeof(m));
-        m.Ph = Lb.Ph; m.Pl = Lb.Pl; m.P_rows = Lb.rows; m.P_pitch = Lb.Kp;
         m.Qh = P.Gh; m.Ql = P.Gl; m.Q_rows = (long long)P.r * P.Qrows; m.Q_pitch = P.Kz;
         m.Kp = P.Kz;
-        m.Pn = Lb.Pn; m.Pp = Lb.Pp;
         m.Qn = Lb.d; m.Qp = P.Qrows;
         m.alpha = C(1.0);
         m.beta = C(0.0);
         m.max_split = 1;
-        if (P.b == 1) {
-            m.Bi = d2; m.Bo = P.r; m.p_sbi = Lb.Pp; m.q_sbo = P.Qrows;
-        } else {
-            m.Bi = P.r; m.Bo = 1; m.q_sbi = P.Qrows;
-        }
         SplitOut o;
         std::memset(&o, 0, sizeof(o));
         o.hi = La.Ph + 2 * P.base;
         o.lo = La.Pl + 2 * P.base;
         o.pd = BIG;
-        o.qd = BIG;
-        const int a = P.a, b = P.b;
-        if (a == 0 && b == 1) {
-            o.sp1 = 1; o.sq1 = K2; o.sbi = (long long)d1 * K2; o.sbo = d0;
-        } else if (a == 0 && b == 2) {
-            o.pd = d0; o.sp1 = 1; o.sp2 = K2; o.sq1 = (long long)d1 * K2; o.sbi = d0;
-        } else if (a == 1 && b == 0) {
-            o.pd = d1; o.sp1 = 1; o.sp2 = (long long)La.Pp * K2; o.sq1 = K2; o.sbi = d1;
-        } else if (a == 1 && b == 2) {
-            o.pd = d0; o.sp1 = K2; o.sp2 = 1; o.sq1 = (long long)La.Pp * K2; o.sbi = d1;
-        } else if (a == 2 && b == 0) {
-            o.pd = d1; o.sp1 = (long long)d0 * K2; o.sp2 = 1; o.sq1 = K2; o.sbi = d2;
-        } else {   // a == 2, b == 1
-            o.sp1 = K2; o.sq1 = (long long)d0 * K2; o.sbi = 1; o.sbo = d2;
+        o.sp1 = 1;
+        if (P.trans) {
+            // X with leg a's index fastest: rows (x fastest, then y), K = leg b
+            SplitPackArgs xa;
+            std::memset(&xa, 0, sizeof(xa));
+            xa.src = x;
+            xa.Ko = 1;
+            xa.Bo = 1;
+            if (b == 0) {          // (a, b) = (2, 0): rows c + d2 b'
+                xa.R = d2; xa.s_r = (long long)d0 * d1; xa.Bi = d1; xa.s_bi = d0; xa.Ki = d0; xa.s_ki = 1;
+            } else if (b == 1) {   // (2, 1): rows c + d2 a
+                xa.R = d2; xa.s_r = (long long)d0 * d1; xa.Bi = d0; xa.s_bi = 1; xa.Ki = d1; xa.s_ki = d0;
+            } else {               // (1, 2): rows b + d1 a
+                xa.R = d1; xa.s_r = d0; xa.Bi = d0; xa.s_bi = 1; xa.Ki = d2; xa.s_ki = (long long)d0 * d1;
+            }
+            xa.Rpad = xa.R;
+            xa.rb_i = xa.R;
+            xa.Kc = S.d[b];
+            xa.pitch = P.Kz;
+            xa.hi = P.Xh;
+            xa.lo = P.Xl;
+            {
+                ProfScope ps(c, PK_PACK, 0.0, (double)xa.R * xa.Bi * S.d[b] * 32.0);
+                c->stats[3] += split_pack(xa, c->stream);
+            }
+            m.Ph = P.Xh; m.Pl = P.Xl; m.P_rows = P.XPp; m.P_pitch = P.Kz;
+            m.Pn = P.Xrows; m.Pp = P.XPp;
+            m.Bi = P.r; m.Bo = 1; m.q_sbi = P.Qrows;
+            o.sbi = S.d[a];
+            if (b == 0) {
+                o.pd = d2; o.sp2 = (long long)d0 * K2; o.sq = K2;
+            } else if (b == 1) {
+                o.pd = d2; o.sp2 = K2; o.sq = (long long)d0 * K2;
+            } else {
+                o.pd = d1; o.sp2 = K2; o.sq = (long long)La.Pp * K2;
+            }
+        } else {
+            m.Ph = Lb.Ph; m.Pl = Lb.Pl; m.P_rows = Lb.rows; m.P_pitch = Lb.Kp;
+            m.Pn = Lb.Pn; m.Pp = Lb.Pp;
+            if (b == 1) {          // (0, 1): p = a, bi = c, q = b', bo = i
+                m.Bi = d2; m.Bo = P.r; m.p_sbi = Lb.Pp; m.q_sbo = P.Qrows;
+                o.sq = K2; o.sbi = (long long)d1 * K2; o.sbo = d0;
+            } else {
+                m.Bi = P.r; m.Bo = 1; m.q_sbi = P.Qrows;
+                if (b == 2) {      // (0, 2): p = a + d0 b, q = c', bi = i
+                    o.pd = d0; o.sp2 = K2; o.sq = (long long)d1 * K2; o.sbi = d0;
+                } else {           // (1, 0): p = b + d1 c, q = a', bi = i
+                    o.pd = d1; o.sp2 = (long long)La.Pp * K2; o.sq = K2; o.sbi = d1;
+                }
+            }
         }
         m.out = &o;
-        const double fl = 8.0 * Lb.Pn * (double)Lb.d * Lb.d * (P.b == 1 ? (double)d2 * P.r : (double)P.r);
+        const double fl = 8.0 * (double)m.Pn * m.Bi * m.Bo * Lb.d * Lb.d;
         ProfScope ps(c, PK_TC, fl, 0.0);
-        ps.shape[0] = Lb.Pn; ps.shape[1] = Lb.d; ps.shape[2] = Lb.d; ps.shape[3] = m.Bi * m.Bo;
+        ps.shape[0] = m.Pn; ps.shape[1] = Lb.d; ps.shape[2] = Lb.d; ps.shape[3] = m.Bi * m.Bo;
         int n = split_mma(m, flag, nullptr, 0, c->stream);
         if (n < 0) throw TtnError(TTN_ERR_CUDA, "split channel contraction launch failed");
         c->stats[3] += n;
@@ -874,8 +942,116 @@ void ensure_env_capacity(ttn_ctx* c, Env& E, size_t nn, size_t nd) {
     }
 }
 
+// Split-precision renormalisation of an operator stack (a2): for every op_i
+// on leg u, E_i = X^H (op_i x_u X) contracted over the legs other than o.
+// The intermediate Z_i = op_i x_u X goes straight from the contraction
+// epilogue into TF32 planes laid out for the projection, whose rows are
+// (leg-o index, i) and whose K runs over (w, u) with w the third leg, w
+// fastest (so that consecutive rows of the first contraction -- X packed with
+// leg w fastest -- land next to each other).  Returns false when the shape
+// does not fill the tensor-core tiles (the caller then runs the FP64 or
+// generic split contractions).  Uses the H_eff planes as scratch: no Krylov
+// run is in flight while environments are rebuilt.
+bool renorm_stack_split(ttn_ctx* c, const cplx* X, const int* d, int u, int o, const cplx* ops, int nop,
+                        cplx* out) {
+    if (c->prec != TTN_SPLIT_TF32X3 || g_force_fp64 || nop < 1) return false;
+    const int w = 3 - u - o;
+    const int du = d[u], dO = d[o], dw = d[w];
+    if (du < 16 || dO < 16 || (long long)dw * dO < 64) return false;
+    const long long s = (long long)d[0] * d[1] * d[2];
+    const long long st[3] = {1, d[0], (long long)d[0] * d[1]};
+    const long long DDu = (long long)du * du, DDo = (long long)dO * dO;
+    const int Kz = (2 * du + SPLIT_BK - 1) / SPLIT_BK * SPLIT_BK;           // K' of op x_u X
+    const long long Kproj = s / dO;                                          // complex K of the projection
+    const int Kp = (int)((2 * Kproj + SPLIT_BK - 1) / SPLIT_BK * SPLIT_BK);
+    const int Qrows_u = (2 * du + SPLIT_BN - 1) / SPLIT_BN * SPLIT_BN;
+    const int Qrows_o = (2 * dO + SPLIT_BN - 1) / SPLIT_BN * SPLIT_BN;
+    const int Pz = dw * dO, Pzp = (Pz + SPLIT_BM - 1) / SPLIT_BM * SPLIT_BM;
+    int chunk = (int)std::max<long long>(1, c->zcap / s);
+    chunk = std::min(chunk, nop);
+    const int Pproj_max = (int)((dO * (long long)chunk + SPLIT_BM - 1) / SPLIT_BM * SPLIT_BM);
+    // buffers: X for the first contraction, the op stack, X^H, the projection's P side
+    const size_t xe = (size_t)Pzp * Kz, oe = (size_t)nop * Qrows_u * Kz, ce = (size_t)Qrows_o * Kp,
+                 pe = (size_t)Pproj_max * Kp;
+    grow_zeroed(c, c->shX[0], c->shX_cap[0], 2 * xe * sizeof(float));
+    grow_zeroed(c, c->shG[0], c->shG_cap[0], 2 * oe * sizeof(float));
+    grow_zeroed(c, c->shQ[0], c->shQ_cap[0], 2 * ce * sizeof(float));
+    grow_zeroed(c, c->shP[0], c->shP_cap[0], 2 * pe * sizeof(float));
+    float *Xh = c->shX[0], *Xl = Xh + xe, *Oh = c->shG[0], *Ol = Oh + oe, *Ch = c->shQ[0], *Cl = Ch + ce,
+          *Ph = c->shP[0], *Pl = Ph + pe;
+    SplitPackArgs a;
+    // X with rows w + dw * o-index, K = u-index
+    std::memset(&a, 0, sizeof(a));
+    a.src = X; a.R = dw; a.s_r = st[w]; a.Bi = dO; a.s_bi = st[o]; a.rb_i = dw; a.Bo = 1;
+    a.Ki = du; a.s_ki = st[u]; a.Ko = 1; a.Rpad = dw; a.Kc = Kz / 2; a.pitch = Kz; a.hi = Xh; a.lo = Xl;
+    c->stats[3] += split_pack(a, c->stream);
+    // op stack, embedded: rows = new u-index, K = old u-index, one padded block per op
+    std::memset(&a, 0, sizeof(a));
+    a.src = ops; a.R = du; a.s_r = 1; a.Ki = du; a.s_ki = du; a.Ko = 1; a.Bi = nop; a.s_bi = DDu; a.Bo = 1;
+    a.rb_i = Qrows_u; a.embed = 1; a.Rpad = Qrows_u / 2; a.Kc = Kz / 2; a.pitch = Kz; a.hi = Oh; a.lo = Ol;
+    c->stats[3] += split_pack(a, c->stream);
+    // X^H, embedded: rows = o-index, K = w + dw * u
+    std::memset(&a, 0, sizeof(a));
+    a.src = X; a.R = dO; a.s_r = st[o]; a.Ki = dw; a.s_ki = st[w]; a.Ko = du; a.s_ko = st[u]; a.Bi = a.Bo = 1;
+    a.conj = 1; a.embed = 1; a.Rpad = Qrows_o / 2; a.Kc = Kp / 2; a.pitch = Kp; a.hi = Ch; a.lo = Cl;
+    c->stats[3] += split_pack(a, c->stream);
+    int* flag = split_flag(c);
+    for (int i0 = 0; i0 < nop; i0 += chunk) {
+        const int nb = std::min(chunk, nop - i0);
+        // Z_i = op_i x_u X into the projection's planes: row o-index + dO i, K w + dw u'
+        SplitMma m;
+        std::memset(&m, 0, sizeof(m));
+        m.Ph = Xh; m.Pl = Xl; m.P_rows = Pzp; m.P_pitch = Kz;
+        m.Qh = Oh + (size_t)i0 * Qrows_u * Kz; m.Ql = Ol + (size_t)i0 * Qrows_u * Kz;
+        m.Q_rows = (long long)nb * Qrows_u; m.Q_pitch = Kz;
+        m.Kp = Kz;
+        m.Pn = Pz; m.Pp = Pzp; m.Qn = du; m.Qp = Qrows_u;
+        m.Bi = nb; m.Bo = 1; m.q_sbi = Qrows_u;
+        m.alpha = C(1.0);
+        m.beta = C(0.0);
+        m.max_split = 1;
+        SplitOut so;
+        std::memset(&so, 0, sizeof(so));
+        const long long K2 = Kp / 2;
+        so.hi = Ph; so.lo = Pl; so.pd = dw; so.sp1 = 1; so.sp2 = K2; so.sq = dw; so.sbi = (long long)dO * K2;
+        m.out = &so;
+        {
+            ProfScope ps(c, PK_TC, 8.0 * (double)Pz * du * du * nb, 0.0);
+            ps.shape[0] = Pz; ps.shape[1] = du; ps.shape[2] = du; ps.shape[3] = nb;
+            int n = split_mma(m, flag, nullptr, 0, c->stream);
+            if (n < 0) throw TtnError(TTN_ERR_CUDA, "split renormalisation launch failed");
+            c->stats[3] += n;
+        }
+        // E_i(k, k') = sum conj(X(..k..)) Z_i(..k'..): P rows k' + dO i, Q rows k
+        SplitMma pj;
+        std::memset(&pj, 0, sizeof(pj));
+        const int Pn = dO * nb, Pp = (Pn + SPLIT_BM - 1) / SPLIT_BM * SPLIT_BM;
+        pj.Ph = Ph; pj.Pl = Pl; pj.P_rows = Pp; pj.P_pitch = Kp;
+        pj.Qh = Ch; pj.Ql = Cl; pj.Q_rows = Qrows_o; pj.Q_pitch = Kp;
+        pj.Kp = Kp;
+        pj.Pn = Pn; pj.Pp = Pp; pj.Qn = dO; pj.Qp = Qrows_o;
+        pj.Bi = pj.Bo = 1;
+        pj.C = out + (long long)i0 * DDo;
+        pj.c_pd = dO; pj.c_p = dO; pj.c_p2 = DDo; pj.c_q = 1;
+        pj.alpha = C(1.0);
+        pj.beta = C(0.0);
+        pj.max_split = SPLIT_K_MAX;
+        const size_t pb = split_mma_partials(pj);
+        if (c->split_cap < 256 + pb) grow_split_ws(c, 256 + pb);
+        flag = reinterpret_cast<int*>(c->split_ws);
+        ProfScope ps(c, PK_TC, 8.0 * (double)Pn * dO * Kproj, 0.0);
+        ps.shape[0] = Pn; ps.shape[1] = dO; ps.shape[2] = (int)Kproj; ps.shape[3] = 1;
+        int n = split_mma(pj, flag, reinterpret_cast<uint8_t*>(c->split_ws) + 256, c->split_cap - 256, c->stream);
+        if (n < 0) throw TtnError(TTN_ERR_CUDA, "split projection launch failed");
+        c->stats[3] += n;
+    }
+    return true;
+}
+
 // op stack (nop matrices of D_u^2) on leg u of X -> projected stack on leg o
 void renorm_stack(ttn_ctx* c, const cplx* X, const int* d, int u, int o, const cplx* ops, int nop, cplx* out) {
+    if (nop < 1) return;
+    if (renorm_stack_split(c, X, d, u, o, ops, nop, out)) return;
     long long s = (long long)d[0] * d[1] * d[2];
     long long DDu = (long long)d[u] * d[u], DDo = (long long)d[o] * d[o];
     int chunk = (int)std::max<long long>(1, c->zcap / s);
@@ -930,7 +1106,9 @@ void renormalize(ttn_ctx* c, const cplx* X, const int* d, int o, const Env& eu, 
     E.has_H = (hbs[u] || hbs[v] || np > 0);
     if (E.has_H) {
         cplx* W = c->tmp[2];
-        heff_apply(c, d, hbs, Dl, pairs, np, X, W);
+        SplitHeff S;
+        if (split_heff_prepare(c, S, d, hbs, pairs, np)) split_heff_apply(c, S, X, W);
+        else heff_apply(c, d, hbs, Dl, pairs, np, X, W);
         project(c, X, d, W, d, o, E.H, 1, 0, 0);
     }
     // one-site operators
@@ -1657,6 +1835,7 @@ void ttn_destroy(ttn_ctx* c) {
         if (c->shP[i]) cudaFree(c->shP[i]);
         if (c->shQ[i]) cudaFree(c->shQ[i]);
         if (c->shG[i]) cudaFree(c->shG[i]);
+        if (c->shX[i]) cudaFree(c->shX[i]);
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->hflag) cudaFreeHost(c->hflag);
@@ -2250,6 +2429,68 @@ ttn_status ttn_selftest_fp64_peak(int method, double* tflops) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         *tflops = fl / (t * 1e-3) / 1e12;
+    });
+}
+
+ttn_status ttn_svd_truncate(const double* A, int M, int N, int chi, double eps, double* U, double* S, double* Vh,
+                            int* k_out, double* discarded) {
+    if (!A || !U || !S || !Vh || !k_out || M < 1 || N < 1 || N > MAX_CHI || M < N || chi < 1 || !(eps >= 0.0) ||
+        (long long)M * N > (1LL << 26))
+        return TTN_ERR_ARG;
+    ttn_ctx tmp;
+    return guard(&tmp, [&] {
+        struct Free {
+            ttn_ctx* t;
+            ~Free() {
+                for (void* p : t->allocs) cudaFree(p);
+                t->allocs.clear();
+            }
+        } fr{&tmp};
+        QrScratch q;
+        alloc_qr_scratch(&tmp, M, N, q);
+        cplx* dA = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)M * N);
+        cplx* dR = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)N * N);
+        cplx* dV = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)N * N);
+        cplx* dUr = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)N * N);
+        cplx* dVh = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)N * N);
+        cplx* dU = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)M * N);
+        double* dS = (double*)dalloc(&tmp, sizeof(double) * N);
+        int* dorder = (int*)dalloc(&tmp, sizeof(int) * N);
+        int* dk = (int*)dalloc(&tmp, sizeof(int) * 4);
+        double* ddisc = (double*)dalloc(&tmp, sizeof(double));
+        unsigned* bar = (unsigned*)dalloc(&tmp, sizeof(unsigned) * 4);
+        int* err = (int*)dalloc(&tmp, sizeof(int) * 4);
+        int* info = (int*)dalloc(&tmp, sizeof(int) * 4);
+        int* cand = (int*)dalloc(&tmp, sizeof(int) * M);
+        std::vector<int> hc(M);
+        for (int i = 0; i < M; ++i) hc[i] = i;
+        CUDA_OK(cudaMemcpy(cand, hc.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemcpy(dA, A, sizeof(cplx) * (size_t)M * N, cudaMemcpyHostToDevice));
+        CUDA_OK(cudaMemset(err, 0, sizeof(int) * 4));
+        int ndep = 0;
+        if (qr_cgs2(dA, M, N, dR, cand, M, q, nullptr, &ndep) < 0)
+            throw TtnError(TTN_ERR_TIMEOUT, "QR grid barrier wait timed out");
+        if (svd_jacobi_square(dR, dV, N, 60, 1e-15, bar, err, info, nullptr) < 0)
+            throw TtnError(TTN_ERR_CUDA, "Jacobi SVD launch failed");
+        int herr = 0;
+        CUDA_OK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) throw TtnError(TTN_ERR_TIMEOUT, "Jacobi SVD grid barrier wait timed out");
+        svd_finish(dR, dV, N, chi, eps, dUr, dVh, dS, dk, ddisc, dorder, nullptr);
+        int k = 0;
+        CUDA_OK(cudaMemcpy(&k, dk, sizeof(int), cudaMemcpyDeviceToHost));
+        GemmArgs g = base_args();   // U = Q Ur
+        g.M = M; g.N = k; g.Ki = N;
+        g.A = dA; g.a_m = 1; g.a_ki = M;
+        g.B = dUr; g.b_ki = 1; g.b_n = N;
+        g.C = dU; g.c_m = 1; g.c_n = M;
+        launch_zgemm_f64(g, nullptr);
+        CUDA_OK(cudaDeviceSynchronize());
+        CUDA_OK(cudaGetLastError());
+        CUDA_OK(cudaMemcpy(U, dU, sizeof(cplx) * (size_t)M * k, cudaMemcpyDeviceToHost));
+        CUDA_OK(cudaMemcpy(S, dS, sizeof(double) * k, cudaMemcpyDeviceToHost));
+        CUDA_OK(cudaMemcpy(Vh, dVh, sizeof(cplx) * (size_t)k * N, cudaMemcpyDeviceToHost));
+        if (discarded) CUDA_OK(cudaMemcpy(discarded, ddisc, sizeof(double), cudaMemcpyDeviceToHost));
+        *k_out = k;
     });
 }
 

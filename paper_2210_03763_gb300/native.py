@@ -64,6 +64,8 @@ SIGNATURES = [
                                                   ctypes.c_int, _I, ctypes.POINTER(ctypes.c_float)]),
     ("ttn_selftest_fp64_peak", ctypes.c_int, [ctypes.c_int, _D]),
     ("ttn_test_inject", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong]),
+    ("ttn_svd_truncate", ctypes.c_int, [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D, _D,
+                                        _I, _D]),
 ]
 
 # fault-injection hooks of ttn_test_inject
@@ -150,6 +152,29 @@ def fp64_peak(method=0):
     if st != 0:
         raise TTNError(st, "selftest_fp64_peak(%d)" % method)
     return float(out[0])
+
+
+def svd_truncate(A, chi, eps=0.0):
+    """Truncated SVD of a host complex M x N matrix (M >= N) on the device:
+    returns (U (M x k), S (k), Vh (k x N), discarded weight)."""
+    lib = load()
+    A = np.asfortranarray(np.asarray(A, dtype=np.complex128))
+    M, N = A.shape
+    kmax = min(chi, N)
+    U = np.zeros((M, kmax), dtype=np.complex128, order="F")
+    S = np.zeros(kmax)
+    Vh = np.zeros((kmax, N), dtype=np.complex128, order="F")
+    k = ctypes.c_int(0)
+    disc = ctypes.c_double(0.0)
+    st = lib.ttn_svd_truncate(A.ctypes.data_as(_D), M, N, int(chi), float(eps), U.ctypes.data_as(_D), _dptr(S),
+                              Vh.ctypes.data_as(_D), ctypes.byref(k), ctypes.byref(disc))
+    if st != 0:
+        raise TTNError(st, "svd_truncate(%d, %d, %d)" % (M, N, chi))
+    n = k.value
+    # U and Vh were written densely with k columns / rows
+    Uk = U.reshape(-1, order="F")[:M * n].reshape(M, n, order="F")
+    Vk = Vh.reshape(-1, order="F")[:n * N].reshape(n, N, order="F")
+    return Uk, S[:n], Vk, disc.value
 
 
 def inject(kind, value=0):
