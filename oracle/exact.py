@@ -7,6 +7,11 @@ the TDVP step uses (reading A8).  The exponential is NOT a Krylov method:
 
 * N <= 6: dense Hermitian eigendecomposition (numpy.linalg.eigh),
 * N <= 9: scipy.sparse.linalg.expm_multiply (Al-Mohy & Higham truncated Taylor).
+
+Decay (Eq. 3, the open-system Hamiltonian of Sec. "Modeling 88Sr quantum
+computers"): with ``gamma`` > 0 the generator is H_OQS = H - i gamma sum_i n_i
+(the no-jump evolution of a decay out of the computational states); the
+dense path then uses scipy.linalg.expm (the generator is not Hermitian).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -48,13 +53,23 @@ def diagonal_interaction(V):
     return d
 
 
-def hamiltonian(V, schedule, t):
-    """Sparse H(t) of Eq. 1 on the full 3^N space."""
+def rydberg_count(n):
+    """Number of atoms in |r> for every product basis state."""
+    idx = np.arange(3 ** n)
+    return sum(((idx // 3 ** i) % 3 == 2).astype(np.float64) for i in range(n))
+
+
+def hamiltonian(V, schedule, t, gamma=0.0):
+    """Sparse H(t) of Eq. 1 on the full 3^N space (minus i gamma sum_i n_i,
+    Eq. 3, when gamma != 0)."""
     n = V.shape[0]
     if n > MAX_ATOMS:
         raise ValueError("exact oracle is limited to %d atoms" % MAX_ATOMS)
     ox, oz, w, de = model.coefficients(schedule, n, t)
-    H = sp.diags(diagonal_interaction(V).astype(np.complex128), format="csr")
+    diag = diagonal_interaction(V).astype(np.complex128)
+    if gamma != 0.0:
+        diag = diag - 1j * gamma * rydberg_count(n)
+    H = sp.diags(diag, format="csr")
     for i in range(n):
         h = model.local_term(ox[i], oz[i], w[i], de[i])
         if not np.any(h):
@@ -67,20 +82,23 @@ def hamiltonian(V, schedule, t):
     return H.tocsr()
 
 
-def step(psi, V, schedule, t, dt):
+def step(psi, V, schedule, t, dt, gamma=0.0):
     """One piecewise-constant step exp(-i H(t+dt/2) dt) psi."""
-    H = hamiltonian(V, schedule, t + 0.5 * dt)
+    H = hamiltonian(V, schedule, t + 0.5 * dt, gamma)
     n = V.shape[0]
     if n <= 6:
+        if gamma != 0.0:
+            from scipy.linalg import expm
+            return expm(-1j * dt * H.toarray()) @ psi
         w, U = np.linalg.eigh(H.toarray())
         return U @ (np.exp(-1j * dt * w) * (U.conj().T @ psi))
     return spla.expm_multiply(-1j * dt * H, psi)
 
 
-def evolve(psi, V, schedule, t0, dt, n_steps):
+def evolve(psi, V, schedule, t0, dt, n_steps, gamma=0.0):
     t = t0
     for _ in range(n_steps):
-        psi = step(psi, V, schedule, t, dt)
+        psi = step(psi, V, schedule, t, dt, gamma)
         t += dt
     return psi
 
@@ -96,5 +114,6 @@ def expectation_local(psi, n_atoms, op):
 
 
 def energy(psi, V, schedule, t):
+    """<psi|H(t)|psi> of the Hermitian H of Eq. 1 (no decay term)."""
     H = hamiltonian(V, schedule, t)
     return float(np.real(np.vdot(psi, H @ psi)))

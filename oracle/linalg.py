@@ -96,14 +96,23 @@ def tridiag_expm_e1(alpha, beta, z):
     return U @ (np.exp(z * lam) * U[0, :])
 
 
-def krylov_expm(apply_H, v0, z, tol=KRYLOV_TOL, m_max=KRYLOV_MMAX, stats=None):
-    """exp(z H) v0 for Hermitian H given as a function, z = -i tau or +i tau.
+def hessenberg_expm_e1(Hm, z):
+    """exp(z H_m) e_1 for a small upper Hessenberg H_m (scipy.linalg.expm)."""
+    from scipy.linalg import expm
+    return expm(z * np.asarray(Hm, dtype=np.complex128))[:, 0]
 
-    Lanczos with full re-orthogonalisation (two classical Gram-Schmidt passes
-    against the whole basis).  alpha_j = Re(<v_j, H v_j>) summed over both
-    passes, beta_j = norm of the residual.  After step j the small problem
-    c = exp(z T_j) e_1 is solved and the run stops when
+
+def krylov_expm(apply_H, v0, z, tol=KRYLOV_TOL, m_max=KRYLOV_MMAX, stats=None, hermitian=True):
+    """exp(z H) v0 for H given as a function, z = -i tau or +i tau.
+
+    Hermitian H: Lanczos with full re-orthogonalisation (two classical
+    Gram-Schmidt passes against the whole basis).  alpha_j = Re(<v_j, H v_j>)
+    summed over both passes, beta_j = norm of the residual.  After step j the
+    small problem c = exp(z T_j) e_1 is solved and the run stops when
     beta_j * |c_j| <= tol (Saad's a-posteriori estimate) or j = m_max.
+    Non-Hermitian H (``hermitian=False``, the open system of Eq. 3): Arnoldi,
+    the same two passes, with column j of the Hessenberg matrix H_j the sum
+    of both passes' projections and H_j(j+1, j) = beta_j; c = exp(z H_j) e_1.
     Returns ||v0|| * sum_i c_i v_i.
     """
     nrm = np.linalg.norm(v0)
@@ -111,6 +120,7 @@ def krylov_expm(apply_H, v0, z, tol=KRYLOV_TOL, m_max=KRYLOV_MMAX, stats=None):
         return np.zeros_like(v0)
     V = [v0 / nrm]
     alpha, beta = [], []
+    Hm = np.zeros((m_max + 1, m_max), dtype=np.complex128)
     c = None
     for j in range(m_max):
         w = apply_H(V[j])
@@ -122,7 +132,12 @@ def krylov_expm(apply_H, v0, z, tol=KRYLOV_TOL, m_max=KRYLOV_MMAX, stats=None):
             w = w - hi * vi
         alpha.append(float(np.real(h1[j] + h2[j])))
         b = float(np.linalg.norm(w))
-        c = tridiag_expm_e1(alpha, beta, z)
+        if hermitian:
+            c = tridiag_expm_e1(alpha, beta, z)
+        else:
+            Hm[:j + 1, j] = h1 + h2
+            c = hessenberg_expm_e1(Hm[:j + 1, :j + 1], z)
+        Hm[j + 1, j] = b
         err = b * abs(c[-1])
         if err <= tol or j == m_max - 1:
             if stats is not None:

@@ -68,19 +68,20 @@ def contract_conj(X, W, leg):
     return np.tensordot(X.conj(), W, axes=(others, others))
 
 
-def block_hamiltonian(env, coef):
-    """H_block(t) = static part + sum over atoms of the drive terms of Eq. 1."""
+def block_hamiltonian(env, coef, gamma=0.0):
+    """H_block(t) = static part + sum over atoms of the drive terms of Eq. 1,
+    and -i gamma n_i for every atom when the decay of Eq. 3 is on."""
     ox, oz, w, de = coef
     H = env.H.copy()
     for i in env.sites:
         if ("rp", i) not in env.ops:       # drive operators not kept: atom never driven
             assert ox[i] == 0 and oz[i] == 0 and w[i] == 0, "drive on atom %d without its operators" % i
-            H -= de[i] * env.ops[("n", i)]
+            H -= (de[i] + 1j * gamma) * env.ops[("n", i)]
             continue
         rp = env.ops[("rp", i)]
         H += (ox[i] * env.ops[("sx", i)] + oz[i] * env.ops[("sz", i)]
               + w[i] * rp + np.conj(w[i]) * rp.conj().T
-              - de[i] * env.ops[("n", i)])
+              - (de[i] + 1j * gamma) * env.ops[("n", i)])
     return H
 
 
@@ -143,6 +144,7 @@ class OracleTTN:
         self.V = model.pair_couplings(xy, C6, r_cut)
         self.schedule = None
         self.t = 0.0
+        self.gamma = 0.0        # decay rate of Eq. 3 (0: closed system)
         keep = None if drive_atoms is None else set(int(a) for a in drive_atoms)
         self.phys = [physical_env(a, keep is None or a in keep) for a in self.tree.leaf_atom]
         self.T = [None] * self.tree.n_nodes
@@ -155,6 +157,11 @@ class OracleTTN:
     def set_hamiltonian(self, xy, C6, r_cut=0.0):
         self.V = model.pair_couplings(xy, C6, r_cut)
         self.rebuild_envs()
+
+    def set_decay(self, gamma):
+        """H_OQS = H - i gamma sum_i n_i (Eq. 3): the no-jump evolution of a
+        decay out of the computational states; Krylov turns to Arnoldi."""
+        self.gamma = float(gamma)
 
     def set_schedule(self, schedule):
         self.schedule = None if schedule is None else np.asarray(schedule, float).reshape(-1, 8)
@@ -248,7 +255,7 @@ class OracleTTN:
     # ------------------------------------------------------------ local maps
     def heff_setup(self, k, coef):
         envs = [self.env(k, u) for u in range(3)]
-        Hb = [block_hamiltonian(e, coef) for e in envs]
+        Hb = [block_hamiltonian(e, coef, self.gamma) for e in envs]
         ch = []
         for u, v in ((0, 1), (0, 2), (1, 2)):
             for n_i, G in channel_list(envs[u], envs[v], self.V):
@@ -267,13 +274,13 @@ class OracleTTN:
         Hb, ch = self.heff_setup(k, coef)
         shape = self.T[k].shape
         f = lambda x: self.heff_apply(x.reshape(shape), Hb, ch).ravel()
-        self.T[k] = krylov_expm(f, self.T[k].ravel(), -1j * tau,
-                                stats=self.krylov_stats).reshape(shape)
+        self.T[k] = krylov_expm(f, self.T[k].ravel(), -1j * tau, stats=self.krylov_stats,
+                                hermitian=self.gamma == 0.0).reshape(shape)
 
     def link_evolve(self, R, env_r, env_c, tau, coef):
         """R <- exp(+i tau H_link) R, H_link R = Hr R + R Hc^T + sum_i n_i R G_i^T."""
-        Hr = block_hamiltonian(env_r, coef)
-        Hc = block_hamiltonian(env_c, coef)
+        Hr = block_hamiltonian(env_r, coef, self.gamma)
+        Hc = block_hamiltonian(env_c, coef, self.gamma)
         ch = channel_list(env_r, env_c, self.V)
         shape = R.shape
 
@@ -283,7 +290,8 @@ class OracleTTN:
             for n_i, G in ch:
                 Y = Y + n_i @ X @ G.T
             return Y.ravel()
-        return krylov_expm(f, R.ravel(), 1j * tau, stats=self.krylov_stats).reshape(shape)
+        return krylov_expm(f, R.ravel(), 1j * tau, stats=self.krylov_stats,
+                           hermitian=self.gamma == 0.0).reshape(shape)
 
     # ---------------------------------------------------------------- sweeps
     def _children_nodes(self, k):
