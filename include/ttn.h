@@ -99,6 +99,15 @@ ttn_status ttn_set_precision(ttn_ctx* ctx, ttn_precision p);
  * non-finite values -> TTN_ERR_ARG.  Rebuilds the environments. */
 ttn_status ttn_set_hamiltonian(ttn_ctx* ctx, const double* xy, double C6, double r_cut);
 
+/* Open system (Eq. 3, Sec. "Modeling 88Sr quantum computers"): evolve with
+ * H_OQS = H - i gamma sum_i n_i, the no-jump evolution of a decay from |r>
+ * to states outside the computational space.  The norm then decreases,
+ * d<psi|psi>/dt = -2 gamma sum_i <psi|n_i|psi> (so the lost norm measures the
+ * integrated Rydberg time T_R), and every local exponential runs as an
+ * Arnoldi iteration instead of Lanczos.  gamma = 0 (the default) is the
+ * closed system; gamma < 0 or non-finite -> TTN_ERR_ARG. */
+ttn_status ttn_set_decay(ttn_ctx* ctx, double gamma);
+
 /* Replace the drive schedule by n_segments segments (copied).  Atoms outside
  * [0, N) or t1 < t0 -> TTN_ERR_ARG.  Drives are evaluated at the midpoint of
  * each TDVP step (Sec. "Tensor network simulations": per-layer control). */

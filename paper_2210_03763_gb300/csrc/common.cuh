@@ -21,7 +21,10 @@ struct GemmArgs {
 };
 
 // Launch on `stream`; returns the number of kernels launched (0 if empty).
-int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream);
+// With a workspace of f64_workspace_bytes(g), contractions whose output
+// tiles cannot fill the GPU split K into ranges summed in fixed order.
+int launch_zgemm_f64(const GemmArgs& g, cudaStream_t stream, void* workspace = nullptr, size_t workspace_bytes = 0);
+size_t f64_workspace_bytes(const GemmArgs& g);
 
 // ---- split-precision building blocks (gemm_split.cu) -------------------------
 // Packing of one side of a split contraction into TF32 hi/lo planes: complex
@@ -117,6 +120,7 @@ struct KrylovScalars {
     double err;                     // a-posteriori error estimate
     int    converged;
     int    nonfinite;
+    cplx   hess[KRYLOV_MMAX + 1][KRYLOV_MMAX];   // Arnoldi: Hessenberg matrix H(i, j) at [i][j]
 };
 
 int red_blocks_for(long long n);
@@ -134,17 +138,38 @@ int k_rescale_to_norm(cplx* x, long long n, const double* px, int Gx, const doub
 int k_krylov_start_ex(KrylovScalars* ks, const double* nrm2_partial, long long n, cudaStream_t s);
 int k_krylov_scalars_ex(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial,
                         long long n, int j, double zr, double zi, double tol, cudaStream_t s);
+// Arnoldi step j for a non-Hermitian generator (the decay of Eq. 3): column j
+// of the Hessenberg matrix is h1 + h2, H(j+1, j) = beta_j; c = exp(z H_j) e_1.
+int k_arnoldi_scalars(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial, long long n,
+                      int j, double zr, double zi, double tol, cudaStream_t s);
 int k_combine(const cplx* V, long long ld, int nv, const KrylovScalars* ks, cplx* y,
               long long n, cudaStream_t s);
+
+// ---- small nodes: the whole Krylov exponential in one block -------------------
+// Nodes and links with s <= SMALL_S tensor entries: H_eff as a dense s x s
+// matrix, then Lanczos/Arnoldi, exponential and combination in one launch.
+constexpr int SMALL_S = 96;
+struct SmallPairs {      // channel pairs of a small H_eff (by value into the kernel)
+    int np;
+    int a[3], b[3], r[3];
+    const cplx* Na[3];   // r matrices of D_a^2
+    const cplx* G[3];    // r matrices of D_b^2
+};
+int k_dense_heff(cplx* H, const int* d, const cplx* hb0, const cplx* hb1, const cplx* hb2, const SmallPairs& pp,
+                 cudaStream_t s);
+// status in ks: converged, nonfinite, err; alpha[0] = iterations
+int k_small_krylov(const cplx* H, int n, cplx* x, double zr, double zi, double tol, int mmax, int arnoldi,
+                   KrylovScalars* ks, cudaStream_t s);
 
 // ---- elementwise / assembly ---------------------------------------------------
 int k_permute3(const cplx* x, cplx* y, int d0, int d1, int d2, int p0, int p1, int p2,
                int inverse, cudaStream_t s);
 int k_fill(cplx* x, long long n, cplx v, cudaStream_t s);
 // H = Hs + sum_i coef_i-weighted drive ops (see kernels.cu)
+// (gamma: decay of Eq. 3, adds -i gamma n_i for every site)
 int k_assemble_block(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsites,
                      const int* site_ids, const cplx* dops, int ndriven,
-                     const int* driven_ids, const double* coef, cudaStream_t s);
+                     const int* driven_ids, const double* coef, double gamma, cudaStream_t s);
 int k_check_finite(const cplx* x, long long n, int* flag, cudaStream_t s);
 double k_fp64_probe(int method, int blocks, int iters, double* out, cudaStream_t s);
 // G_i = sum_j W[j + nb*i] N_j, i < r (N: nb matrices of n entries, contiguous;

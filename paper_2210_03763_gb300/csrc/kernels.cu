@@ -294,6 +294,249 @@ __global__ void krylov_scalars_kernel(KrylovScalars* ks, const cplx* h1, const c
     }
 }
 
+// exp(z H) e_1 for the dense m x m matrix H (row-major rows of ld
+// KRYLOV_MMAX in H[i][j]), m <= 31, by the scaled Taylor series as in
+// tridiag_expm_warp: substeps with |z/n_sub| * ||H||_inf <= 1/2.  One warp;
+// lane i holds component i.
+__device__ void hess_expm_warp(const cplx (*Hm)[KRYLOV_MMAX], int m, double zr, double zi, cplx* out) {
+    const int l = threadIdx.x & 31;
+    double rs = 0.0;
+    if (l < m)
+        for (int k = 0; k < m; ++k) {
+            const cplx v = Hm[l][k];
+            rs += sqrt(v.x * v.x + v.y * v.y);
+        }
+    for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, o));
+    const double zn = sqrt(zr * zr + zi * zi);
+    const double want = zn * rs / 0.5;
+    const int nsub = (want >= 1.0 && want < 65536.0) ? (int)ceil(want) : (want >= 65536.0 ? 65536 : 1);
+    const double hr = zr / nsub, hi = zi / nsub;
+    cplx u = make_double2(l == 0 ? 1.0 : 0.0, 0.0);
+    for (int s = 0; s < nsub; ++s) {
+        cplx term = u, sum = u;
+        for (int k = 1; k <= 40; ++k) {
+            double tr = 0.0, ti = 0.0;
+            for (int q = 0; q < m; ++q) {
+                const double xr = __shfl_sync(0xffffffffu, term.x, q);
+                const double xi = __shfl_sync(0xffffffffu, term.y, q);
+                if (l < m) {
+                    const cplx v = Hm[l][q];
+                    tr += v.x * xr - v.y * xi;
+                    ti += v.x * xi + v.y * xr;
+                }
+            }
+            const double inv = 1.0 / k;
+            term = make_double2((hr * tr - hi * ti) * inv, (hr * ti + hi * tr) * inv);
+            sum = cadd(sum, term);
+            double tm = fabs(term.x) + fabs(term.y);
+            double sm = fabs(sum.x) + fabs(sum.y);
+            for (int o = 16; o > 0; o >>= 1) {
+                tm = fmax(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+                sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+            }
+            if (tm <= 1e-18 * sm) break;
+        }
+        u = sum;
+    }
+    if (l < m) out[l] = u;
+}
+
+__global__ void arnoldi_scalars_kernel(KrylovScalars* ks, const cplx* h1, const cplx* h2,
+                                       const double* beta_partial, int G, int j, double zr, double zi, double tol) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i <= j; ++i) ks->hess[i][j] = cadd(h1[i], h2[i]);
+        const double b2 = reduce_norm_partials(beta_partial, G);
+        ks->beta[j] = sqrt(b2);
+        ks->hess[j + 1][j] = make_double2(ks->beta[j], 0.0);
+        ks->alpha[j] = ks->hess[j][j].x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) hess_expm_warp(ks->hess, j + 1, zr, zi, ks->c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double bj = ks->beta[j];
+        const cplx cj = ks->c[j];
+        const double err = bj * sqrt(cj.x * cj.x + cj.y * cj.y);
+        ks->err = err;
+        ks->converged = (err <= tol) ? 1 : 0;
+        ks->inv_scale = bj > 0.0 ? 1.0 / bj : 0.0;
+        if (!isfinite(err) || !isfinite(ks->hess[j][j].x) || !isfinite(ks->hess[j][j].y)) ks->nonfinite = 1;
+    }
+}
+
+// ---------------------------------------------- small nodes: dense H_eff
+// Element (x, y) of the s x s matrix of H_eff for a node (or link) with leg
+// dims d: block terms hb_u (D_u x D_u, nullptr: none) and channel pairs
+// sum_i Na_i (leg a) (x) G_i (leg b), identity on the third leg.
+__global__ void dense_heff_kernel(cplx* H, int d0, int d1, int d2, const cplx* hb0, const cplx* hb1,
+                                  const cplx* hb2, SmallPairs pp) {
+    const int s = d0 * d1 * d2;
+    const long long n = (long long)s * s;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int xr = (int)(e % s), yc = (int)(e / s);
+        const int x[3] = {xr % d0, (xr / d0) % d1, xr / (d0 * d1)};
+        const int y[3] = {yc % d0, (yc / d0) % d1, yc / (d0 * d1)};
+        const int dd[3] = {d0, d1, d2};
+        const cplx* hb[3] = {hb0, hb1, hb2};
+        cplx h = make_double2(0.0, 0.0);
+        for (int u = 0; u < 3; ++u) {
+            if (!hb[u]) continue;
+            bool diag = true;
+            for (int v = 0; v < 3; ++v)
+                if (v != u && x[v] != y[v]) diag = false;
+            if (diag) h = cadd(h, hb[u][x[u] + dd[u] * y[u]]);
+        }
+        for (int p = 0; p < pp.np; ++p) {
+            const int a = pp.a[p], b = pp.b[p], w = 3 - a - b;
+            if (x[w] != y[w]) continue;
+            const long long Da2 = (long long)dd[a] * dd[a], Db2 = (long long)dd[b] * dd[b];
+            const long long ia = x[a] + (long long)dd[a] * y[a], ib = x[b] + (long long)dd[b] * y[b];
+            for (int i = 0; i < pp.r[p]; ++i)
+                h = cadd(h, cmul(pp.Na[p][i * Da2 + ia], pp.G[p][i * Db2 + ib]));
+        }
+        H[e] = h;
+    }
+}
+
+// The whole Krylov exponential x <- exp(z H) x of a small dense H (s <= 96)
+// in one block: Lanczos (or Arnoldi when `arnoldi`) with the same two-pass
+// full re-orthogonalisation, tridiagonal (Hessenberg) exponential and
+// stopping rule as the multi-kernel path, with H and the basis in shared
+// memory.  Small nodes of the tree otherwise spend their time in launches
+// and host round trips, not in arithmetic.  Status goes to ks (converged,
+// nonfinite, err, and alpha[0] holds the iteration count as a double).
+constexpr int SMALL_KRYLOV_THREADS = 256;
+__global__ void __launch_bounds__(SMALL_KRYLOV_THREADS)
+    small_krylov_kernel(const cplx* Hg, int s, cplx* x, double zr, double zi, double tol, int mmax, int arnoldi,
+                        KrylovScalars* ks) {
+    extern __shared__ cplx smem_c[];
+    cplx* Hs = smem_c;                   // s * s, column-major
+    cplx* V = Hs + (long long)s * s;     // (mmax + 1) * s
+    cplx* w = V + (long long)(mmax + 1) * s;
+    __shared__ cplx h1[KRYLOV_MMAX + 1], h2[KRYLOV_MMAX + 1];
+    __shared__ double alpha[32], beta[32], sh_red[SMALL_KRYLOV_THREADS / 32];
+    __shared__ cplx hess[KRYLOV_MMAX + 1][KRYLOV_MMAX];
+    __shared__ cplx c[32];
+    __shared__ double s_nrm0, s_beta;
+    __shared__ int s_done, s_m, s_conv, s_nonfin;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = SMALL_KRYLOV_THREADS / 32;
+    for (long long e = tid; e < (long long)s * s; e += SMALL_KRYLOV_THREADS) Hs[e] = Hg[e];
+    // start vector
+    double a = 0.0;
+    for (int e = tid; e < s; e += SMALL_KRYLOV_THREADS) {
+        const cplx v = x[e];
+        V[e] = v;
+        a += v.x * v.x + v.y * v.y;
+    }
+    a = block_sum_d(a, sh_red);
+    if (tid == 0) {
+        s_nrm0 = sqrt(a);
+        s_done = (s_nrm0 == 0.0);
+        s_nonfin = isfinite(s_nrm0) ? 0 : 1;
+        s_conv = s_done;
+        s_m = 0;
+    }
+    __syncthreads();
+    if (s_done || s_nonfin) {
+        if (tid == 0) {
+            ks->converged = s_conv;
+            ks->nonfinite = s_nonfin;
+            ks->err = 0.0;
+            ks->alpha[0] = 0.0;
+        }
+        return;
+    }
+    const double inv0 = 1.0 / s_nrm0;
+    for (int e = tid; e < s; e += SMALL_KRYLOV_THREADS) V[e] = make_double2(V[e].x * inv0, V[e].y * inv0);
+    __syncthreads();
+    int j = 0;
+    for (;; ++j) {
+        const cplx* vj = V + (long long)j * s;
+        // w = H v_j
+        for (int r = tid; r < s; r += SMALL_KRYLOV_THREADS) {
+            cplx acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < s; ++k) acc = cadd(acc, cmul(Hs[r + (long long)s * k], vj[k]));
+            w[r] = acc;
+        }
+        __syncthreads();
+        // two passes of classical Gram-Schmidt against v_0 .. v_j, one warp per dot
+        for (int pass = 0; pass < 2; ++pass) {
+            cplx* hp = pass == 0 ? h1 : h2;
+            for (int i = warp; i <= j; i += nw) {
+                const cplx* vi = V + (long long)i * s;
+                cplx d = make_double2(0.0, 0.0);
+                for (int e = lane; e < s; e += 32) d = cadd(d, cdotc(vi[e], w[e]));
+                for (int o = 16; o > 0; o >>= 1) {
+                    d.x += __shfl_down_sync(0xffffffffu, d.x, o);
+                    d.y += __shfl_down_sync(0xffffffffu, d.y, o);
+                }
+                if (lane == 0) hp[i] = d;
+            }
+            __syncthreads();
+            for (int e = tid; e < s; e += SMALL_KRYLOV_THREADS) {
+                cplx v = w[e];
+                for (int i = 0; i <= j; ++i) {
+                    const cplx p = cmul(V[(long long)i * s + e], hp[i]);
+                    v.x -= p.x;
+                    v.y -= p.y;
+                }
+                w[e] = v;
+            }
+            __syncthreads();
+        }
+        double b2 = 0.0;
+        for (int e = tid; e < s; e += SMALL_KRYLOV_THREADS) b2 += w[e].x * w[e].x + w[e].y * w[e].y;
+        b2 = block_sum_d(b2, sh_red);
+        if (tid == 0) {
+            s_beta = sqrt(b2);
+            beta[j] = s_beta;
+            alpha[j] = h1[j].x + h2[j].x;
+            if (arnoldi) {
+                for (int i = 0; i <= j; ++i) hess[i][j] = cadd(h1[i], h2[i]);
+                hess[j + 1][j] = make_double2(s_beta, 0.0);
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            if (arnoldi) {
+                hess_expm_warp(hess, j + 1, zr, zi, c);
+            } else {
+                __shared__ double ta[32], tb[32];
+                ta[lane] = lane <= j ? alpha[lane] : 0.0;
+                tb[lane] = lane < j ? beta[lane] : 0.0;
+                __syncwarp();
+                tridiag_expm_warp(ta, tb, j + 1, zr, zi, c);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double err = s_beta * sqrt(c[j].x * c[j].x + c[j].y * c[j].y);
+            s_conv = err <= tol;
+            if (!isfinite(err) || !isfinite(alpha[j])) s_nonfin = 1;
+            s_done = s_conv || s_nonfin || j == mmax - 1;
+            ks->err = err;
+        }
+        __syncthreads();
+        if (s_done) break;
+        const double inv = 1.0 / s_beta;
+        cplx* vn = V + (long long)(j + 1) * s;
+        for (int e = tid; e < s; e += SMALL_KRYLOV_THREADS) vn[e] = make_double2(w[e].x * inv, w[e].y * inv);
+        __syncthreads();
+    }
+    // x = |x0| sum_i c_i v_i
+    for (int e = tid; e < s; e += SMALL_KRYLOV_THREADS) {
+        cplx acc = make_double2(0.0, 0.0);
+        for (int i = 0; i <= j; ++i) acc = cadd(acc, cmul(V[(long long)i * s + e], c[i]));
+        x[e] = make_double2(acc.x * s_nrm0, acc.y * s_nrm0);
+    }
+    if (tid == 0) {
+        ks->converged = s_conv;
+        ks->nonfinite = s_nonfin;
+        ks->alpha[0] = (double)(j + 1);
+    }
+}
+
 __global__ void permute3_kernel(const cplx* x, cplx* y, int d0, int d1, int d2, int p0, int p1, int p2,
                                 int inverse) {
     // y has axes (x-axis p0, x-axis p1, x-axis p2), first fastest
@@ -324,7 +567,7 @@ __global__ void fill_kernel(cplx* x, long long n, cplx v) {
 // coef: 5 doubles per atom (omega_x, omega_z, Re W, Im W, delta)
 __global__ void assemble_block_kernel(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsites,
                                       const int* site_ids, const cplx* dops, int ndriven,
-                                      const int* driven_ids, const double* coef) {
+                                      const int* driven_ids, const double* coef, double gamma) {
     long long DD = (long long)D * D;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < DD;
          e += (long long)gridDim.x * blockDim.x) {
@@ -332,11 +575,12 @@ __global__ void assemble_block_kernel(cplx* H, const cplx* Hs, int D, const cplx
         long long et = b + (long long)D * a;           // transposed position
         cplx h = Hs ? Hs[e] : make_double2(0.0, 0.0);
         for (int i = 0; i < nsites; ++i) {
+            // -(Delta_i + i gamma) n_i: detuning, and the decay of Eq. 3
             double de = coef[5 * site_ids[i] + 4];
-            if (de != 0.0) {
+            if (de != 0.0 || gamma != 0.0) {
                 cplx v = nops[i * DD + e];
-                h.x -= de * v.x;
-                h.y -= de * v.y;
+                h.x -= de * v.x - gamma * v.y;
+                h.y -= de * v.y + gamma * v.x;
             }
         }
         for (int q = 0; q < ndriven; ++q) {
@@ -366,7 +610,7 @@ __global__ void check_finite_kernel(const cplx* x, long long n, int* flag) {
 // G_i = sum_j V_ij n_j of an effective Hamiltonian.  One thread per matrix
 // entry keeps up to 16 outputs in registers and reads each N_j entry once per
 // group of 16 outputs (memory bound for the few outputs of a group).
-constexpr int WSUM_GROUP = 16;
+template <int WSUM_GROUP>
 __global__ void weighted_sum_kernel(const cplx* __restrict__ N, int nb, long long n, const double* __restrict__ W,
                                     int r, cplx* __restrict__ G, int staged) {
     extern __shared__ double sw_smem[];
@@ -382,7 +626,8 @@ __global__ void weighted_sum_kernel(const cplx* __restrict__ N, int nb, long lon
             cplx acc[WSUM_GROUP];
 #pragma unroll
             for (int t = 0; t < WSUM_GROUP; ++t) acc[t] = make_double2(0.0, 0.0);
-            for (int j = 0; j < nb; ++j) {
+#pragma unroll 4
+            for (int j = 0; j < nb; ++j) {   // unrolled: several loads in flight per thread
                 const cplx v = N[(long long)j * n + e];
 #pragma unroll
                 for (int t = 0; t < WSUM_GROUP; ++t) {
@@ -512,6 +757,12 @@ int k_krylov_scalars_ex(KrylovScalars* ks, const cplx* h1, const cplx* h2, const
     return 1;
 }
 
+int k_arnoldi_scalars(KrylovScalars* ks, const cplx* h1, const cplx* h2, const double* beta_partial, long long n,
+                      int j, double zr, double zi, double tol, cudaStream_t s) {
+    arnoldi_scalars_kernel<<<1, 32, 0, s>>>(ks, h1, h2, beta_partial, red_blocks_for(n), j, zr, zi, tol);
+    return 1;
+}
+
 int k_permute3(const cplx* x, cplx* y, int d0, int d1, int d2, int p0, int p1, int p2, int inverse,
                cudaStream_t s) {
     long long n = (long long)d0 * d1 * d2;
@@ -526,11 +777,11 @@ int k_fill(cplx* x, long long n, cplx v, cudaStream_t s) {
 }
 
 int k_assemble_block(cplx* H, const cplx* Hs, int D, const cplx* nops, int nsites, const int* site_ids,
-                     const cplx* dops, int ndriven, const int* driven_ids, const double* coef,
+                     const cplx* dops, int ndriven, const int* driven_ids, const double* coef, double gamma,
                      cudaStream_t s) {
     long long DD = (long long)D * D;
     assemble_block_kernel<<<grid_for(DD), 256, 0, s>>>(H, Hs, D, nops, nsites, site_ids, dops, ndriven,
-                                                       driven_ids, coef);
+                                                       driven_ids, coef, gamma);
     return 1;
 }
 
@@ -559,6 +810,29 @@ int k_weighted_sum(const cplx* N, int nb, long long n, const double* W, int r, c
     // small blocks: the work per entry is nb * r FP64 FMAs, so spread the
     // entries over every SM
     const long long blocks = std::min<long long>((n + 63) / 64, 16 * 152);
-    weighted_sum_kernel<<<(unsigned)blocks, 64, staged ? need : 0, s>>>(N, nb, n, W, r, G, staged);
+    if (r <= 4)   // few outputs: small register groups, more loads in flight
+        weighted_sum_kernel<4><<<(unsigned)blocks, 64, staged ? need : 0, s>>>(N, nb, n, W, r, G, staged);
+    else
+        weighted_sum_kernel<16><<<(unsigned)blocks, 64, staged ? need : 0, s>>>(N, nb, n, W, r, G, staged);
+    return 1;
+}
+
+int k_dense_heff(cplx* H, const int* d, const cplx* hb0, const cplx* hb1, const cplx* hb2, const SmallPairs& pp,
+                 cudaStream_t s) {
+    const long long n = (long long)d[0] * d[1] * d[2];
+    dense_heff_kernel<<<grid_for(n * n), 256, 0, s>>>(H, d[0], d[1], d[2], hb0, hb1, hb2, pp);
+    return 1;
+}
+
+int k_small_krylov(const cplx* H, int n, cplx* x, double zr, double zi, double tol, int mmax, int arnoldi,
+                   KrylovScalars* ks, cudaStream_t s) {
+    const size_t smem = sizeof(cplx) * ((size_t)n * n + (size_t)(mmax + 2) * n);
+    static bool attr = false;   // same limit on every device (shared memory per block)
+    if (!attr) {
+        cudaFuncSetAttribute(small_krylov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(cplx) * ((size_t)SMALL_S * SMALL_S + (size_t)(KRYLOV_MMAX + 2) * SMALL_S)));
+        attr = true;
+    }
+    small_krylov_kernel<<<1, SMALL_KRYLOV_THREADS, smem, s>>>(H, n, x, zr, zi, tol, mmax, arnoldi, ks);
     return 1;
 }

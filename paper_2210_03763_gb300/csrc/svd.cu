@@ -7,7 +7,8 @@
 // to |r_i^H r_j| <= tol ||r_i|| ||r_j||.  One sweep visits every pair once in
 // round-robin order (N' - 1 rounds of N'/2 disjoint pairs, N' = N rounded up
 // to even); one cooperative launch runs all sweeps, one block per pair of a
-// round, with a grid barrier between rounds.  Complex rotation of a pair with
+// round, with a grid barrier between rounds (pairs whose inner product is
+// below 1e-30 |R|_F^2 are treated as orthogonal).  Complex rotation of a pair with
 // alpha = |r_i|^2, beta = |r_j|^2, gamma = r_i^H r_j = g e^{i phi}:
 //   zeta = (beta - alpha) / (2 g),  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 //   c = 1 / sqrt(1 + t^2),  s = c t,
@@ -80,6 +81,28 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(cplx* R, cplx* V, i
     __shared__ double rot[4];   // c, s, cos phi, sin phi; rot[0] < 0: skip
     const unsigned nb = gridDim.x;
     const int k = blockIdx.x;
+    // |R|_F^2, the same in every block (same summation order): pairs whose
+    // inner product is below 1e-30 |R|_F^2 are left alone -- columns that
+    // rank deficiency has already reduced to rounding noise would otherwise
+    // be rotated into denormals and overflow the rotation angle
+    __shared__ double s_floor;
+    {
+        double a = 0.0;
+        for (long long e = threadIdx.x; e < (long long)N * N; e += SVD_THREADS) {
+            const cplx x = __ldcg(R + e);
+            a += x.x * x.x + x.y * x.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < SVD_THREADS / 32; ++q) t += red[0][q];
+            s_floor = 1e-30 * t;
+        }
+        __syncthreads();
+    }
+    const double floor_g = s_floor;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         int* cnt = &info[2 + (sweep & 1)];
@@ -97,8 +120,10 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(cplx* R, cplx* V, i
                 const cplx* ci = R + (long long)i * N;
                 const cplx* cj = R + (long long)j * N;
                 double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
+                // columns move between blocks from round to round: read them
+                // through L2 (__ldcg), never from a stale L1 line
                 for (int e = threadIdx.x; e < N; e += SVD_THREADS) {
-                    const cplx x = ci[e], y = cj[e];
+                    const cplx x = __ldcg(ci + e), y = __ldcg(cj + e);
                     a += x.x * x.x + x.y * x.y;
                     b += y.x * y.x + y.y * y.y;
                     gr += x.x * y.x + x.y * y.y;   // conj(x) y
@@ -128,7 +153,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(cplx* R, cplx* V, i
                         Gi += redi[q];
                     }
                     const double g = sqrt(Gr * Gr + Gi * Gi);
-                    if (g > tol * sqrt(A * B) && g > 0.0) {
+                    if (g > tol * sqrt(A * B) && g > floor_g) {
                         const double zeta = (B - A) / (2.0 * g);
                         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                         const double c = 1.0 / sqrt(1.0 + t * t);
@@ -149,7 +174,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(cplx* R, cplx* V, i
                         cplx* xi = X + (long long)i * N;
                         cplx* xj = X + (long long)j * N;
                         for (int e = threadIdx.x; e < N; e += SVD_THREADS) {
-                            const cplx x = xi[e], y = xj[e];
+                            const cplx x = __ldcg(xi + e), y = __ldcg(xj + e);
                             const cplx yp = make_double2(pc * y.x + ps * y.y, pc * y.y - ps * y.x);   // e^{-i phi} y
                             xi[e] = make_double2(c * x.x - s * yp.x, c * x.y - s * yp.y);
                             xj[e] = make_double2(s * x.x + c * yp.x, s * x.y + c * yp.y);

@@ -116,6 +116,7 @@ struct ttn_ctx {
 
     std::vector<double> xy;
     double C6 = 0.0, r_cut = 0.0;
+    double gamma = 0.0;                    // decay rate of Eq. 3 (0: closed system)
     std::vector<double> V;                 // N x N
     std::vector<ttn_pulse> schedule;
     std::vector<int> driven;               // per atom
@@ -132,6 +133,7 @@ struct ttn_ctx {
     long long gcap = 0;
     cplx* hb[3] = {nullptr, nullptr, nullptr};
     cplx* Rbuf = nullptr;
+    cplx* dense_H = nullptr;  // SMALL_S^2: dense H_eff of a small node or link
     cplx* Kbasis = nullptr;   // (KRYLOV_MMAX + 1) * smax
     KrylovScalars* ks = nullptr;
     cplx* kh1 = nullptr;      // KRYLOV_MMAX + 1
@@ -158,6 +160,8 @@ struct ttn_ctx {
     size_t ev_next = 0;
     void* split_ws = nullptr;   // packed operands of the split GEMM (+ error flag)
     size_t split_cap = 0;
+    void* f64_ws = nullptr;     // split-K partial sums of FP64 contractions
+    size_t f64_cap = 0;
     // split-precision H_eff of one node visit (see SplitHeff): per leg the
     // stacked operand planes [X | channel stacks] and the operator stack,
     // per channel pair the packed G stack; grown on demand, zeroed when
@@ -320,8 +324,21 @@ void gemm(ttn_ctx* c, const GemmArgs& g) {
         }
     }
     if (n < 0) {
+        const size_t wb = f64_workspace_bytes(g);
+        if (wb > c->f64_cap) {   // split-K partials of small-output FP64 contractions
+            CUDA_OK(cudaStreamSynchronize(c->stream));
+            if (c->f64_ws) cudaFree(c->f64_ws);
+            c->f64_ws = nullptr;
+            c->f64_cap = 0;
+            const size_t want = wb + wb / 4;
+            if (test_take_alloc_fail() || cudaMalloc(&c->f64_ws, want) != cudaSuccess) {
+                c->f64_ws = nullptr;
+                throw TtnError(TTN_ERR_ALLOC, "FP64 split-K workspace");
+            }
+            c->f64_cap = want;
+        }
         ProfScope ps(c, PK_F64, fl, 0.0, &g);
-        n = launch_zgemm_f64(g, c->stream);
+        n = launch_zgemm_f64(g, c->stream, c->f64_ws, c->f64_cap);
     }
     c->stats[3] += n;
 }
@@ -877,7 +894,8 @@ void split_heff_apply(ttn_ctx* c, const SplitHeff& S, const cplx* x, cplx* y) {
 
 void assemble(ttn_ctx* c, const Env& e, cplx* out) {
     c->stats[3] += k_assemble_block(out, e.has_H ? e.H : nullptr, e.D, e.nops, (int)e.sites.size(),
-                                    e.d_sites, e.dops, (int)e.driven.size(), e.d_driven, c->d_coef, c->stream);
+                                    e.d_sites, e.dops, (int)e.driven.size(), e.d_driven, c->d_coef, c->gamma,
+                                    c->stream);
 }
 
 bool env_has_block(const Env& e) { return e.has_H || !e.sites.empty(); }
@@ -905,7 +923,10 @@ void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
         cplx* part2 = c->kpart + (size_t)RED_BLOCKS * (KRYLOV_MMAX + 1);
         c->stats[3] += k_orth_update_ex(V, ld, j + 1, c->kpart, w, n, 1, part2, nullptr, c->kh1, 0, -1, s);
         c->stats[3] += k_orth_update_ex(V, ld, j + 1, part2, w, n, 2, nullptr, c->kpn, c->kh2, 0, -1, s);
-        c->stats[3] += k_krylov_scalars_ex(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
+        if (c->gamma != 0.0)   // non-Hermitian generator (decay): Arnoldi
+            c->stats[3] += k_arnoldi_scalars(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
+        else
+            c->stats[3] += k_krylov_scalars_ex(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
         CUDA_OK(cudaMemcpyAsync(c->hflag, &c->ks->converged, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         c->hflag[2] = 0;
         if (c->split_ws)   // a tensor-core wait that gave up leaves garbage: report it first
@@ -924,6 +945,47 @@ void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
     }
     c->stats[0] += 1;
     c->stats[3] += k_combine(V, ld, j + 1, c->ks, x, n, s);
+}
+
+// Small nodes and links (s <= SMALL_S): H_eff as a dense matrix and the whole
+// Krylov exponential in one launch (same algorithm and stopping rule as
+// krylov()), with one host round trip for the status instead of one per
+// Lanczos step.
+bool small_evolve(ttn_ctx* c, const int* d, cplx* const* hb, const Pair* pairs, int np, cplx* x, double zr,
+                  double zi) {
+    const long long s = (long long)d[0] * d[1] * d[2];
+    if (s > SMALL_S) return false;
+    SmallPairs pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.np = np;
+    for (int p = 0; p < np; ++p) {
+        pp.a[p] = pairs[p].a;
+        pp.b[p] = pairs[p].b;
+        pp.r[p] = pairs[p].r;
+        pp.Na[p] = pairs[p].Na;
+        pp.G[p] = pairs[p].G;
+    }
+    const double tol = (c->prec == TTN_FP64) ? 1e-13 : 1e-9;
+    c->stats[3] += k_dense_heff(c->dense_H, d, hb[0], hb[1], hb[2], pp, c->stream);
+    c->stats[3] += k_small_krylov(c->dense_H, (int)s, x, zr, zi, tol, test_krylov_mmax(), c->gamma != 0.0 ? 1 : 0,
+                                  c->ks, c->stream);
+    struct {
+        double alpha0;
+        double err;
+        int flags[2];
+    } st;
+    CUDA_OK(cudaMemcpyAsync(&st.alpha0, &c->ks->alpha[0], sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaMemcpyAsync(&st.err, &c->ks->err, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaMemcpyAsync(st.flags, &c->ks->converged, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    if (st.flags[1]) throw TtnError(TTN_ERR_NUMERIC, "non-finite value in Lanczos");
+    c->stats[0] += 1;
+    c->stats[1] += (int64_t)st.alpha0;
+    if (!st.flags[0]) {
+        c->max_err = std::max(c->max_err, st.err);
+        if (st.err > 1e-6) throw TtnError(TTN_ERR_KRYLOV, "Lanczos did not converge in m_max steps");
+    }
+    return true;
 }
 
 // ------------------------------------------------------ renormalisation
@@ -1208,6 +1270,7 @@ void node_evolve(ttn_ctx* c, int k, double tau) {
     }
     Pair pairs[3];
     int np = setup_pairs(c, e, pairs);
+    if (small_evolve(c, nd.d, hbs, pairs, np, c->T[k], 0.0, -tau)) return;
     SplitHeff S;
     const bool sp = split_heff_prepare(c, S, nd.d, hbs, pairs, np);
     krylov(c, c->T[k], nd.s, 0.0, -tau, [&](const cplx* x, cplx* y) {
@@ -1229,6 +1292,7 @@ void link_evolve(ttn_ctx* c, const Env& er, const Env& ec, double tau) {
         }
     Pair pairs[3];
     int np = setup_pairs(c, e, pairs);
+    if (small_evolve(c, d, hbs, pairs, np, c->Rbuf, 0.0, tau)) return;
     SplitHeff S;
     const bool sp = split_heff_prepare(c, S, d, hbs, pairs, np);
     krylov(c, c->Rbuf, (long long)d[0] * d[1], 0.0, tau, [&](const cplx* x, cplx* y) {
@@ -1497,6 +1561,7 @@ void allocate(ttn_ctx* c) {
     for (int i = 0; i < 3; ++i) c->Gbuf[i] = (cplx*)dalloc(c, sizeof(cplx) * gc);
     for (int i = 0; i < 3; ++i) c->hb[i] = (cplx*)dalloc(c, sizeof(cplx) * MAX_CHI * MAX_CHI);
     c->Rbuf = (cplx*)dalloc(c, sizeof(cplx) * MAX_CHI * MAX_CHI);
+    c->dense_H = (cplx*)dalloc(c, sizeof(cplx) * SMALL_S * SMALL_S);
     c->Kbasis = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1) * c->smax);
     c->ks = (KrylovScalars*)dalloc(c, sizeof(KrylovScalars));
     c->kh1 = (cplx*)dalloc(c, sizeof(cplx) * (KRYLOV_MMAX + 1));
@@ -1831,6 +1896,7 @@ void ttn_destroy(ttn_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (void* p : c->allocs) cudaFree(p);
     if (c->split_ws) cudaFree(c->split_ws);
+    if (c->f64_ws) cudaFree(c->f64_ws);
     for (int i = 0; i < 3; ++i) {
         if (c->shP[i]) cudaFree(c->shP[i]);
         if (c->shQ[i]) cudaFree(c->shQ[i]);
@@ -1872,6 +1938,12 @@ ttn_status ttn_set_hamiltonian(ttn_ctx* c, const double* xy, double C6, double r
         rebuild_up_envs(c);
         sync_check(c);
     });
+}
+
+ttn_status ttn_set_decay(ttn_ctx* c, double gamma) {
+    if (!c || !std::isfinite(gamma) || gamma < 0.0) return TTN_ERR_ARG;
+    c->gamma = gamma;
+    return TTN_OK;
 }
 
 ttn_status ttn_apply_pulse(ttn_ctx* c, const ttn_pulse* sched, int n) {
@@ -2293,6 +2365,8 @@ ttn_status ttn_selftest_contract(int M, int N, int K, int precision, unsigned lo
         tmp.allocs.clear();
         if (tmp.split_ws) cudaFree(tmp.split_ws);
         tmp.split_ws = nullptr;
+        if (tmp.f64_ws) cudaFree(tmp.f64_ws);
+        tmp.f64_ws = nullptr;
     });
 }
 
@@ -2360,6 +2434,8 @@ ttn_status ttn_selftest_contract_host(const double* A, const double* B, double* 
                 t->allocs.clear();
                 if (t->split_ws) cudaFree(t->split_ws);
                 t->split_ws = nullptr;
+                if (t->f64_ws) cudaFree(t->f64_ws);
+                t->f64_ws = nullptr;
             }
         } fr{&tmp};
         cplx* dA = (cplx*)dalloc(&tmp, sizeof(cplx) * (size_t)M * K);

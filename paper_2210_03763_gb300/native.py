@@ -31,6 +31,7 @@ SIGNATURES = [
     ("ttn_set_precision", ctypes.c_int, [_P, ctypes.c_int]),
     ("ttn_set_hamiltonian", ctypes.c_int, [_P, _D, ctypes.c_double, ctypes.c_double]),
     ("ttn_apply_pulse", ctypes.c_int, [_P, _P, ctypes.c_int]),
+    ("ttn_set_decay", ctypes.c_int, [_P, ctypes.c_double]),
     ("ttn_set_product_state", ctypes.c_int, [_P, _D]),
     ("ttn_set_ghz_target", ctypes.c_int, [_P, _I, ctypes.c_double]),
     ("ttn_tdvp_step", ctypes.c_int, [_P, ctypes.c_double]),
@@ -245,6 +246,10 @@ class TTN:
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(self.N, 2)
         self._check(self.lib.ttn_set_hamiltonian(self.h, _dptr(xy), float(C6), float(r_cut)),
                     "set_hamiltonian")
+
+    def set_decay(self, gamma):
+        """H - i gamma sum_i n_i (the open system of Eq. 3); 0 = closed."""
+        self._check(self.lib.ttn_set_decay(self.h, float(gamma)), "set_decay")
 
     def apply_pulse(self, schedule):
         from .workloads import to_pulse_array

@@ -9,11 +9,14 @@ r_G = sqrt(8) a no layer holds two CZ gates; rotations run beside the CZ),
 each shifted so that the
 24 steps straddle the end of the control atoms' pi pulse and the start of
 the target atoms' 2 pi pulse (t = T_L/4 - 0.6 .. T_L/4 + 0.6 of the layer),
-starting from a seeded random product state so that every pair interaction
-is active.
+starting from a seeded random TTN with every bond at full rank (random
+isometries, workloads.random_ttn_tensors): every pair interaction is active
+and no QR of the sweep needs the completion of rank-deficient bases, whose
+dependence decisions at the 1e-10 threshold make trajectories from product
+states sensitive to rounding (reading A10).
 24 single-site TDVP steps of dt = 0.05 (plain complex128 oracle).  Stored
 per schedule: the return amplitude <psi(0)|psi(t)> (a gauge-invariant
-functional of the whole state, of order one here), <GHZ|psi> (GHZ target on
+functional of the whole state), <GHZ|psi> (GHZ target on
 all 16 atoms, phase 0), the norm, the energy at the final time and
 <|0><0|>, <|1><1|>, <n> per atom.
 
@@ -29,6 +32,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import numpy as np  # noqa: E402
 
 from oracle import ttn as ottn  # noqa: E402
+from oracle.tree import Tree  # noqa: E402
 from paper_2210_03763_gb300 import workloads as W  # noqa: E402
 
 LX = LY = 4
@@ -53,19 +57,24 @@ def cfg2_schedule(r_G):
     return xy, sched
 
 
+def start_tensors():
+    tr = Tree(LX, LY, CHI)
+    return W.random_ttn_tensors([tr.shape(k) for k in range(tr.n_nodes)], SEED)
+
+
 def main():
     lines = ["# cfg2 trajectories from oracle.ttn.OracleTTN (make_cfg2_trajectories.py)",
              "# lattice %dx%d chi %d C6 %g dt %g steps %d seed %d" % (LX, LY, CHI, C6, DT, STEPS, SEED)]
-    amps = W.random_product_amps(LX * LY, SEED)
+    Ts = start_tensors()
     for name, r_G in SCHEDULES:
         xy, sched = cfg2_schedule(r_G)
         o = ottn.OracleTTN(LX, LY, CHI, xy, C6)
         o.set_schedule(sched)
-        o.set_product_state(amps)
+        o.set_tensors(Ts)
         for _ in range(STEPS):
             o.step(DT)
-        start = ottn.OracleTTN(LX, LY, 1, xy, C6)
-        start.set_product_state(amps)
+        start = ottn.OracleTTN(LX, LY, CHI, xy, C6)
+        start.set_tensors(Ts)
         ret = o.overlap(start)
         tgt = ottn.OracleTTN(LX, LY, 2, xy, C6)
         tgt.set_ghz([1] * (LX * LY), 0.0)

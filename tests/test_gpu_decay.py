@@ -1,0 +1,130 @@
+"""Open system through the C ABI (Eq. 3: H_OQS = H - i gamma sum_i n_i, the
+no-jump evolution of a decay out of the computational states; Arnoldi
+instead of Lanczos) against the CPU oracle:
+
+* exact regime (2x2, chi = 16; 2x3, chi = 81): the TTN equals the exact
+  state vector with decay, |1 - F| <= 1e-10 on the normalised states and the
+  norms to 1e-10;
+* truncated regime (4x4, chi = 12) from identical random tensors: the same
+  algorithm as the oracle's, norm, <n_i> and the state itself to 1e-10;
+* norm loss against the integrated Rydberg population: 1 - N(t) =
+  2 gamma T_R with T_R the trapezoid integral of sum_i <n_i> (TDVP keeps
+  d<psi|psi>/dt = 2 Im <psi|H|psi> = -2 gamma sum <n> because the projected
+  generator acts on psi as H does), to the O(dt^2) of the integrator and of
+  the trapezoid rule (relative 1e-3 at dt = 0.01);
+* split precision with decay tracks the FP64 run (norm 1e-8).
+"""
+import numpy as np
+import pytest
+
+from oracle import exact, model, ttn as ottn
+from paper_2210_03763_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GAMMA = 0.2
+
+
+@pytest.fixture(scope="module")
+def native():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2210_03763_gb300 import native as nat
+    return nat
+
+
+@pytest.mark.parametrize("Lx,Ly,chi", [(2, 2, 16), (2, 3, 81)])
+def test_decay_exact_regime_equals_state_vector(native, Lx, Ly, chi):
+    N = Lx * Ly
+    xy = W.square_lattice(Lx, Ly)
+    sched = W.random_constant_schedule(N, 2)
+    amps = W.random_product_amps(N, 3)
+    g = native.TTN(Lx, Ly, chi)
+    g.set_hamiltonian(xy, 20.0)
+    g.apply_pulse(sched)
+    g.set_decay(GAMMA)
+    g.set_product_state(amps)
+    V = model.pair_couplings(xy, 20.0)
+    psi = exact.product_state(amps)
+    dt = 0.02
+    for s in range(4):
+        g.step(dt)
+        psi = exact.step(psi, V, sched, s * dt, dt, GAMMA)
+    d = g.dense()
+    nd, npsi = np.vdot(d, d).real, np.vdot(psi, psi).real
+    assert npsi < 1 - 1e-3
+    assert abs(1 - abs(np.vdot(psi, d)) ** 2 / (nd * npsi)) < 1e-10
+    assert abs(nd - npsi) < 1e-10
+    assert abs(g.norm() - npsi) < 1e-10
+    g.close()
+
+
+def test_decay_identical_start_same_trajectory(native):
+    Lx = Ly = 4
+    chi = 12
+    xy = W.square_lattice(Lx, Ly)
+    sched = W.random_constant_schedule(16, 5)
+    g = native.TTN(Lx, Ly, chi)
+    g.set_hamiltonian(xy, 20.0)
+    g.apply_pulse(sched)
+    g.set_decay(GAMMA)
+    o = ottn.OracleTTN(Lx, Ly, chi, xy, 20.0)
+    o.set_schedule(sched)
+    o.set_decay(GAMMA)
+    Ts = W.random_ttn_tensors([o.tree.shape(k) for k in range(o.tree.n_nodes)], 11)
+    for k, X in enumerate(Ts):
+        g.set_node(k, X)
+    g.refresh_envs()
+    o.set_tensors(Ts)
+    for _ in range(2):
+        g.step(0.03)
+        o.step(0.03)
+    for k in range(o.tree.n_nodes):
+        assert np.allclose(g.get_node(k), o.T[k], atol=1e-10), k
+    assert abs(g.norm() - o.norm()) < 1e-12
+    assert o.norm() < 1 - 1e-4
+    assert np.allclose(g.measure(2), o.measure(2), atol=1e-11)
+    g.close()
+
+
+def test_norm_loss_is_twice_gamma_rydberg_time(native):
+    Lx, Ly, chi = 4, 4, 32
+    xy = W.square_lattice(Lx, Ly)
+    sched, TL = W.cz_layer_workload(Lx, Ly, 2.0 ** 1.5)
+    g = native.TTN(Lx, Ly, chi)
+    g.set_hamiltonian(xy, 20.0)
+    g.apply_pulse(sched)
+    g.set_decay(GAMMA)
+    g.set_product_state(W.plus_state_amps(16))
+    dt = 0.01
+    pr = [g.measure(2).sum()]
+    for _ in range(60):
+        g.step(dt)
+        pr.append(g.measure(2).sum())
+    TR = dt * (0.5 * pr[0] + sum(pr[1:-1]) + 0.5 * pr[-1])
+    loss = 1.0 - g.norm()
+    assert TR > 1e-3
+    assert abs(loss - 2 * GAMMA * TR) < 1e-3 * loss, (loss, 2 * GAMMA * TR)
+    g.close()
+
+
+def test_split_decay_tracks_fp64(native):
+    Lx, Ly, chi = 4, 4, 64
+    xy = W.square_lattice(Lx, Ly)
+    sched, TL = W.cz_layer_workload(Lx, Ly, 2.0 ** 1.5)
+    runs = []
+    for prec in (native.SPLIT_TF32X3, native.FP64):
+        g = native.TTN(Lx, Ly, chi)
+        g.set_precision(prec)
+        g.set_hamiltonian(xy, 20.0)
+        g.apply_pulse(sched)
+        g.set_decay(GAMMA)
+        g.set_product_state(W.random_product_amps(16, 9))
+        for _ in range(5):
+            g.step(0.02)
+        runs.append(g)
+    a, b = runs
+    assert abs(a.norm() - b.norm()) < 1e-8
+    infid = 1 - abs(a.overlap(b)) ** 2 / (a.norm() * b.norm())
+    assert infid < 1e-10
+    a.close()
+    b.close()
