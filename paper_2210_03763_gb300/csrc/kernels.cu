@@ -344,10 +344,11 @@ __device__ void hess_expm_warp(const cplx (*Hm)[KRYLOV_MMAX], int m, double zr, 
 __global__ void arnoldi_scalars_kernel(KrylovScalars* ks, const cplx* h1, const cplx* h2,
                                        const double* beta_partial, int G, int j, double zr, double zi, double tol) {
     if (threadIdx.x == 0) {
-        for (int i = 0; i <= j; ++i) ks->hess[i][j] = cadd(h1[i], h2[i]);
+        // the whole column j: projections, the subdiagonal beta_j, zeros below
         const double b2 = reduce_norm_partials(beta_partial, G);
         ks->beta[j] = sqrt(b2);
-        ks->hess[j + 1][j] = make_double2(ks->beta[j], 0.0);
+        for (int i = 0; i <= KRYLOV_MMAX; ++i)
+            ks->hess[i][j] = i <= j ? cadd(h1[i], h2[i]) : make_double2(i == j + 1 ? ks->beta[j] : 0.0, 0.0);
         ks->alpha[j] = ks->hess[j][j].x;
     }
     __syncthreads();
@@ -492,10 +493,9 @@ __global__ void __launch_bounds__(SMALL_KRYLOV_THREADS)
             s_beta = sqrt(b2);
             beta[j] = s_beta;
             alpha[j] = h1[j].x + h2[j].x;
-            if (arnoldi) {
-                for (int i = 0; i <= j; ++i) hess[i][j] = cadd(h1[i], h2[i]);
-                hess[j + 1][j] = make_double2(s_beta, 0.0);
-            }
+            if (arnoldi)   // the whole column j: projections, beta_j, zeros below
+                for (int i = 0; i <= KRYLOV_MMAX; ++i)
+                    hess[i][j] = i <= j ? cadd(h1[i], h2[i]) : make_double2(i == j + 1 ? s_beta : 0.0, 0.0);
         }
         __syncthreads();
         if (warp == 0) {
