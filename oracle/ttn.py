@@ -418,3 +418,73 @@ class OracleTTN:
         order = np.argsort(keep)
         Y = np.transpose(Y, order)
         return Y.reshape(-1, order="F")
+
+
+# ------------------------------------------------------------- truncation
+def bond_grams(o):
+    """G_k(a, a') = <R_a|R_a'> for the parent bond of every non-root node k,
+    where |psi> = sum_a |L_a> |R_a> with |L_a> the orthonormal subtree states
+    (canonical form, centre at the root).  Top-down: the root's dummy leg
+    has G = [[1]], and for node k, child u of p,
+    G_k(a, a') = sum over p's other legs of conj(X_p(..a..)) (G_p x_2 X_p)(..a'..)."""
+    tr = o.tree
+    G = {tr.root: np.ones((1, 1), dtype=np.complex128)}
+    for lev in reversed(tr.level_nodes):
+        for p in lev:
+            W = apply_leg(G[p], o.T[p], 2)
+            for u, (kind, k) in enumerate(tr.children[p]):
+                if kind == "node":
+                    G[k] = contract_conj(o.T[p], W, u)
+    return G
+
+
+def compress(o, chi_new):
+    """Truncation of every bond to the new tree's dimensions (bond dimension
+    chi_new, Sec. "Tensor network simulations"): the kept basis of the parent
+    bond of node k is the top eigenvectors U_k of its bond Gram G_k (the
+    Schmidt basis of that bipartition); X_k <- U_c^H on its child legs, U_k
+    on its parent leg (all bonds projected at once), then QR bottom-up
+    restores the canonical form (centre at the root).  Returns the new
+    OracleTTN and the discarded weight of every bond,
+    sum of dropped eigenvalues / trace."""
+    tr = o.tree
+    new = OracleTTN(tr.Lx, tr.Ly, chi_new)
+    new.V = o.V
+    new.schedule = o.schedule
+    new.gamma = o.gamma
+    new.t = o.t
+    nt = new.tree
+    G = bond_grams(o)
+    U, disc = {}, {}
+    for k in range(tr.n_nodes):
+        if k == tr.root:
+            continue
+        lam, vec = np.linalg.eigh(G[k])
+        order = np.argsort(-lam, kind="stable")
+        lam, vec = lam[order], vec[:, order]
+        # G_k is the transpose of the bond's reduced density matrix: its
+        # eigenvectors are the conjugates of the Schmidt vectors
+        keep = nt.dim[k]
+        U[k] = vec[:, :keep].conj()
+        tot = np.sum(np.clip(lam, 0, None))
+        disc[k] = float(np.sum(np.clip(lam[keep:], 0, None)) / tot) if tot > 0 else 0.0
+    T = []
+    for k in range(tr.n_nodes):
+        X = o.T[k]
+        for u, (kind, c) in enumerate(tr.children[k]):
+            if kind == "node":
+                X = apply_leg(U[c].conj().T, X, u)
+        if k != tr.root:
+            X = apply_leg(U[k].T, X, 2)
+        T.append(X)
+    # canonical form: QR of every non-root node towards its parent, bottom-up
+    for lev in nt.level_nodes:
+        for k in lev:
+            if k == nt.root:
+                continue
+            T[k], R = qr_leg(T[k], 2, new.allowed(k))
+            p = nt.parent[k]
+            u = 0 if nt.children[p][0] == ("node", k) else 1
+            T[p] = apply_leg(R, T[p], u)
+    new.set_tensors(T)
+    return new, disc
