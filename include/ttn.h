@@ -151,6 +151,40 @@ ttn_status ttn_get_dense(ttn_ctx* ctx, double* psi);
 ttn_status ttn_save(ttn_ctx* ctx, const char* path);
 ttn_status ttn_load(ttn_ctx* ctx, const char* path);
 
+/* Truncate the state of src to the bond dimensions of dst (Sec. "Tensor
+ * network simulations": the bond dimension chi controls the kept
+ * entanglement): dst must have the same lattice and no bond larger than
+ * src's.  Every bond is projected on the top eigenvectors of its bond Gram
+ * (the Schmidt basis of the bipartition the bond cuts, from the canonical
+ * form of src), all at once, computed on the GPU by one-sided Jacobi; dst is
+ * then brought to canonical form by QR.  dst's Hamiltonian and schedule are
+ * its own; its time is set to src's.  discarded (may be NULL) receives 2
+ * doubles: the sum over bonds and the largest of the discarded weights
+ * (dropped eigenvalues / trace of the bond density matrix).  The infidelity
+ * of the truncation is at most (sum_bonds sqrt(weight))^2. */
+ttn_status ttn_compress(ttn_ctx* src, ttn_ctx* dst, double* discarded);
+
+/* Projective measurement of every atom in the {|0>, |1>, |r>} basis, n_shots
+ * times (Sec. "Parallel quantum algorithms": measurement histograms of many
+ * shots).  Each shot measures the atoms one after another in the tree's leaf
+ * order (ttn_leaf_atoms, padding leaves skipped) and draws atom i's outcome
+ * from its conditional distribution given the outcomes already drawn, by
+ * inverse transform sampling: outcome s is the first level with
+ * u < (P(0) + ... + P(s)) / (P(0) + P(1) + P(2)).
+ *   uniforms : host, n_shots x N doubles in [0, 1), row-major, column j the
+ *              j-th real atom in leaf order (the caller draws them; equal
+ *              uniforms give equal outcomes on equal states);
+ *   outcomes : host, n_shots x N ints (0: |0>, 1: |1>, 2: |r>), column =
+ *              atom id.
+ * The walk runs on the GPU, batched over shots: depth first, entering a
+ * subtree with the Gram of its conditioned complement and leaving it with
+ * the amplitude vector of its drawn outcomes.  The contractions use the
+ * context's precision (split precision can flip a draw whose uniform lies
+ * within ~1e-7 of a boundary).  Moves the orthogonality centre to the root
+ * (the state is unchanged).  n_shots = 0 does nothing; n_shots < 0, NULL
+ * buffers -> TTN_ERR_ARG; allocation failure -> TTN_ERR_ALLOC. */
+ttn_status ttn_sample(ttn_ctx* ctx, const double* uniforms, int n_shots, int* outcomes);
+
 /* ---- introspection used by tests and tools ------------------------------ */
 ttn_status ttn_num_nodes(const ttn_ctx* ctx, int* n);
 /* dims[3] = (d0, d1, d2); children[2] = child node ids, or -(leaf+1) for a leaf. */

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libttn.so")
-SOURCES = ["ttn.cu", "gemm_f64.cu", "gemm_split.cu", "kernels.cu", "qr.cu", "noalloc.cu", "svd.cu"]
+SOURCES = ["ttn.cu", "gemm_f64.cu", "gemm_split.cu", "kernels.cu", "qr.cu", "noalloc.cu", "svd.cu", "sample.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I" + os.path.join(HERE, "..", "include")]

@@ -219,10 +219,22 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand,
 int svd_jacobi_square(cplx* R, cplx* V, int N, int max_sweeps, double tol, unsigned* bar, int* err, int* info,
                       cudaStream_t s);
 // sigma_i = |r_i|, descending order, kept k = min(chi, #{sigma >= eps sigma_max})
-// (at least 1), discarded weight sum_{t >= k} sigma^2 / sum sigma^2;
+// (at least 1; eps < 0: exactly min(chi, N), zero values included),
+// discarded weight sum_{t >= k} sigma^2 / sum sigma^2;
 // Ur (N x k) = normalised kept columns, Vh (k x N) = their conj(V) rows.
 int svd_finish(const cplx* R, const cplx* V, int N, int chi, double eps, cplx* Ur, cplx* Vh, double* S, int* k,
                double* disc, int* order, cudaStream_t s);
+
+// ---- measurement sampling (sample.cu) ---------------------------------------------
+// S shots, one matrix / vector per shot at stride ld (complex):
+// G_b /= max(Re tr G_b, 1e-300); w_b /= |w_b| (when nonzero); the draw of one
+// leaf (atom < 0: padding, outcome 0 without a uniform) from diag(G_b) (3 x 3,
+// stride 9) with uniform U[b * ldu + j], outcome into out[b * N + atom],
+// w_b (stride 3) = e_outcome.
+int k_trace_normalize(cplx* G, int D, long long ld, int S, cudaStream_t s);
+int k_vec_normalize(cplx* w, int D, long long ld, int S, cudaStream_t s);
+int k_leaf_draw(const cplx* G, const double* U, long long ldu, int j, int atom, int* out, int N, cplx* w, int S,
+                cudaStream_t s);
 
 // ---- test hooks (ttn_test_inject in ttn.cu) -----------------------------------
 // Stall time in ns for the next tensor-core launch (0: none; consumes one

@@ -220,7 +220,11 @@ __global__ void svd_finish_kernel(const cplx* R, const cplx* V, int N, int chi, 
     if (threadIdx.x == 0) {
         smax = sig[order[0]];
         int n = 0;
-        while (n < N && n < chi && sig[order[n]] >= eps * smax && sig[order[n]] > 0.0) ++n;
+        if (eps < 0.0) {   // keep exactly min(chi, N) columns, zero values included
+            n = chi < N ? chi : N;
+        } else {
+            while (n < N && n < chi && sig[order[n]] >= eps * smax && sig[order[n]] > 0.0) ++n;
+        }
         if (n == 0) n = 1;
         k = n;
         tot = 0.0;

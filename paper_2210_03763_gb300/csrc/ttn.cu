@@ -19,6 +19,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <stdexcept>
 #include <string>
@@ -2567,6 +2568,264 @@ ttn_status ttn_svd_truncate(const double* A, int M, int N, int chi, double eps, 
         CUDA_OK(cudaMemcpy(Vh, dVh, sizeof(cplx) * (size_t)k * N, cudaMemcpyDeviceToHost));
         if (discarded) CUDA_OK(cudaMemcpy(discarded, ddisc, sizeof(double), cudaMemcpyDeviceToHost));
         *k_out = k;
+    });
+}
+
+ttn_status ttn_compress(ttn_ctx* src, ttn_ctx* dst, double* discarded) {
+    if (!src || !dst || src == dst || src->Lx != dst->Lx || src->Ly != dst->Ly ||
+        src->nodes.size() != dst->nodes.size())
+        return TTN_ERR_ARG;
+    for (size_t k = 0; k < src->nodes.size(); ++k)
+        for (int u = 0; u < 3; ++u)
+            if (dst->nodes[k].d[u] > src->nodes[k].d[u]) return TTN_ERR_ARG;
+    return guard(dst, [&] {
+        ForceFp64 f64;
+        ttn_ctx* c = src;
+        centre_to_root(c);
+        CUDA_OK(cudaStreamSynchronize(c->stream));
+        const int nn = (int)c->nodes.size();
+        std::vector<void*> temp;
+        struct Free {
+            std::vector<void*>& t;
+            ~Free() {
+                for (void* p : t) cudaFree(p);
+            }
+        } fr{temp};
+        auto tmalloc = [&](size_t bytes) {
+            void* p = nullptr;
+            if (test_take_alloc_fail() || cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess)
+                throw TtnError(TTN_ERR_ALLOC, "compress buffers");
+            temp.push_back(p);
+            return p;
+        };
+        // bond Grams top-down: G_k(a, a') = <R_a|R_a'>, G_root = [[1]]
+        std::vector<cplx*> G(nn, nullptr);
+        G[c->root] = (cplx*)tmalloc(sizeof(cplx));
+        const cplx one = C(1.0);
+        CUDA_OK(cudaMemcpyAsync(G[c->root], &one, sizeof(cplx), cudaMemcpyHostToDevice, c->stream));
+        for (int li = (int)c->level_nodes.size() - 1; li >= 0; --li)
+            for (int p : c->level_nodes[li]) {
+                const Node& np_ = c->nodes[p];
+                leg_apply(c, G[p], np_.d[2], c->T[p], np_.d, 2, c->tmp[0], 0.0);
+                for (int u = 0; u < 2; ++u) {
+                    const int k = np_.child[u];
+                    if (k < 0) continue;
+                    const long long D = np_.d[u];
+                    G[k] = (cplx*)tmalloc(sizeof(cplx) * D * D);
+                    project(c, c->T[p], np_.d, c->tmp[0], np_.d, u, G[k], 1, 0, 0);
+                }
+            }
+        // Schmidt bases: one-sided Jacobi on each Gram (Hermitian PSD: its left
+        // singular vectors are its eigenvectors), all D columns in descending
+        // order; the kept ones are the first D' (their conjugates in the
+        // subtree basis)
+        unsigned* bar = (unsigned*)tmalloc(sizeof(unsigned) * 4);
+        int* err = (int*)tmalloc(sizeof(int) * 4);
+        int* info = (int*)tmalloc(sizeof(int) * 4);
+        int* order = (int*)tmalloc(sizeof(int) * MAX_CHI);
+        int* dk = (int*)tmalloc(sizeof(int) * 4);
+        double* ddisc = (double*)tmalloc(sizeof(double));
+        double* dS = (double*)tmalloc(sizeof(double) * MAX_CHI);
+        cplx* Rw = (cplx*)tmalloc(sizeof(cplx) * MAX_CHI * MAX_CHI);
+        cplx* Vw = (cplx*)tmalloc(sizeof(cplx) * MAX_CHI * MAX_CHI);
+        cplx* Vh = (cplx*)tmalloc(sizeof(cplx) * MAX_CHI * MAX_CHI);
+        std::vector<cplx*> UT(nn, nullptr), UHc(nn, nullptr);   // U^T (no conj) and conj(U)^T per bond
+        CUDA_OK(cudaMemsetAsync(err, 0, sizeof(int) * 4, c->stream));
+        double dsum = 0.0, dmax = 0.0;
+        std::vector<double> hS(MAX_CHI);
+        for (int k = 0; k < nn; ++k) {
+            if (k == c->root) continue;
+            const int D = c->nodes[k].d[2], Dn = dst->nodes[k].d[2];
+            CUDA_OK(cudaMemcpyAsync(Rw, G[k], sizeof(cplx) * D * D, cudaMemcpyDeviceToDevice, c->stream));
+            if (svd_jacobi_square(Rw, Vw, D, 60, 1e-15, bar, err, info, c->stream) < 0)
+                throw TtnError(TTN_ERR_CUDA, "Jacobi launch failed");
+            cplx* Ur = (cplx*)tmalloc(sizeof(cplx) * D * D);
+            svd_finish(Rw, Vw, D, D, -1.0, Ur, Vh, dS, dk, ddisc, order, c->stream);
+            int herr = 0;
+            CUDA_OK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CUDA_OK(cudaMemcpyAsync(hS.data(), dS, sizeof(double) * D, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_OK(cudaStreamSynchronize(c->stream));
+            if (herr) throw TtnError(TTN_ERR_TIMEOUT, "Jacobi grid barrier wait timed out");
+            double tot = 0.0, drop = 0.0;   // eigenvalues of the Gram are its singular values
+            for (int t = 0; t < D; ++t) {
+                tot += hS[t];
+                if (t >= Dn) drop += hS[t];
+            }
+            const double e = tot > 0.0 ? drop / tot : 0.0;
+            dsum += e;
+            dmax = std::max(dmax, e);
+            // Ur: D x D, its first Dn columns are the kept eigenvectors of G_k;
+            // transpose them to Dn x D (the leg matrices below)
+            UT[k] = (cplx*)tmalloc(sizeof(cplx) * Dn * D);
+            c->stats[3] += k_permute3(Ur, UT[k], D, Dn, 1, 1, 0, 2, 0, c->stream);
+        }
+        // projected tensors: children legs by U_c^H = Ur_c^T, parent leg by
+        // U_k^T = conj(Ur_k)^T, then into dst
+        for (int k = 0; k < nn; ++k) {
+            const Node& nd = c->nodes[k];
+            int d[3] = {nd.d[0], nd.d[1], nd.d[2]};
+            const cplx* cur = c->T[k];
+            cplx* bufs[2] = {c->tmp[0], c->tmp[1]};
+            int bi = 0;
+            for (int u = 0; u < 2; ++u) {
+                const int ch = nd.child[u];
+                if (ch < 0) continue;
+                const int Dn = dst->nodes[ch].d[2];
+                leg_apply(c, UT[ch], Dn, cur, d, u, bufs[bi], 0.0);
+                d[u] = Dn;
+                cur = bufs[bi];
+                bi ^= 1;
+            }
+            if (k != c->root) {
+                const int Dn = dst->nodes[k].d[2];
+                leg_apply(c, UT[k], Dn, cur, d, 2, bufs[bi], 0.0, 1, 0, 0, true);
+                d[2] = Dn;
+                cur = bufs[bi];
+            }
+            const long long sz = (long long)d[0] * d[1] * d[2];
+            CUDA_OK(cudaMemcpyAsync(dst->T[k], cur, sizeof(cplx) * sz, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        CUDA_OK(cudaStreamSynchronize(c->stream));
+        // canonical form of dst: QR of every non-root node towards its parent, bottom-up
+        for (auto& lev : dst->level_nodes)
+            for (int k : lev) {
+                if (k == dst->root) continue;
+                const int p = dst->nodes[k].parent;
+                const int u = dst->nodes[p].child[0] == k ? 0 : 1;
+                qr_leg(dst, k, 2);
+                absorb(dst, p, u, true);
+            }
+        dst->t = src->t;
+        dst->centre = dst->root;
+        rebuild_up_envs(dst);
+        sync_check(dst);
+        if (discarded) {
+            discarded[0] = dsum;
+            discarded[1] = dmax;
+        }
+    });
+}
+
+// Projective sampling: the depth-first walk of every shot, batched over the
+// shots of a batch.  Entering node k with the Gram Gamma_b (parent leg, D x D,
+// column-major, trace 1) of shot b's conditioned complement:
+//   child 0 : G0_b(c0, c0') = sum_{c1, a, a'} conj X(c0, c1, a) Gamma_b(a, a') X(c0', c1, a')
+//             (the c1 subtree is unmeasured and isometric, so it contracts to
+//             the identity), walk child 0 -> amplitude vector w0_b(c0);
+//   child 1 : Y_b(c1, a) = sum_c0 w0_b(c0) X(c0, c1, a),
+//             G1_b(c1, c1') = sum_{a, a'} conj Y_b(c1, a) Gamma_b(a, a') Y_b(c1', a'),
+//             walk child 1 -> w1_b(c1);
+//   leaving : w_b(a) = sum_c1 w1_b(c1) Y_b(c1, a), normalised.
+// A leaf draws from the diagonal of its 3 x 3 Gram and returns e_outcome.
+// The root's Gram is [[1]] (its parent leg is the dummy leg of dimension 1).
+ttn_status ttn_sample(ttn_ctx* c, const double* uniforms, int n_shots, int* outcomes) {
+    if (!c || n_shots < 0 || (n_shots > 0 && (!uniforms || !outcomes))) return TTN_ERR_ARG;
+    if (n_shots == 0) return TTN_OK;
+    return guard(c, [&] {
+        centre_to_root(c);
+        const int nn = (int)c->nodes.size(), nl = (int)c->leaf_atom.size(), N = c->N;
+        std::vector<int> jidx(nl, -1);   // uniform column of each real leaf
+        for (int l = 0, j = 0; l < nl; ++l)
+            if (c->leaf_atom[l] >= 0) jidx[l] = j++;
+        // per-shot device footprint -> shots per batch (about 2 GB per batch)
+        long long per_shot = c->smax + 12LL * nl;
+        for (int k = 0; k < nn; ++k) {
+            const int* d = c->nodes[k].d;
+            per_shot += (long long)d[1] * d[2] + (long long)d[2] * d[2] + d[2];
+        }
+        const long long budget = 2LL << 30;
+        const int S = (int)std::max(1LL, std::min<long long>(n_shots, budget / (16LL * per_shot)));
+        std::vector<void*> temp;
+        struct Free {
+            std::vector<void*>& t;
+            ~Free() {
+                for (void* p : t) cudaFree(p);
+            }
+        } fr{temp};
+        auto tmalloc = [&](size_t bytes) {
+            void* p = nullptr;
+            if (test_take_alloc_fail() || cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess)
+                throw TtnError(TTN_ERR_ALLOC, "sampling buffers");
+            temp.push_back(p);
+            return p;
+        };
+        cplx* Wsc = (cplx*)tmalloc(sizeof(cplx) * (size_t)S * c->smax);
+        std::vector<cplx*> gam(nn), Y(nn), wout(nn), lgam(nl), lw(nl);
+        for (int k = 0; k < nn; ++k) {
+            const int* d = c->nodes[k].d;
+            gam[k] = (cplx*)tmalloc(sizeof(cplx) * (size_t)S * d[2] * d[2]);
+            Y[k] = (cplx*)tmalloc(sizeof(cplx) * (size_t)S * d[1] * d[2]);
+            wout[k] = (cplx*)tmalloc(sizeof(cplx) * (size_t)S * d[2]);
+        }
+        for (int l = 0; l < nl; ++l) {
+            lgam[l] = (cplx*)tmalloc(sizeof(cplx) * 9 * (size_t)S);
+            lw[l] = (cplx*)tmalloc(sizeof(cplx) * 3 * (size_t)S);
+        }
+        double* dU = (double*)tmalloc(sizeof(double) * (size_t)S * N);
+        int* dO = (int*)tmalloc(sizeof(int) * (size_t)S * N);
+        int nb = 0;   // shots in the current batch
+        auto child_gram = [&](const Node& nd, int u) {
+            const int ch = nd.child[u];
+            return ch >= 0 ? gam[ch] : lgam[-ch - 1];
+        };
+        std::function<cplx*(int)> visit;
+        auto walk_child = [&](const Node& nd, int u) -> cplx* {
+            const int ch = nd.child[u];
+            if (ch >= 0) return visit(ch);
+            const int l = -ch - 1;
+            c->stats[3] += k_leaf_draw(lgam[l], dU, N, jidx[l], c->leaf_atom[l], dO, N, lw[l], nb, c->stream);
+            return lw[l];
+        };
+        visit = [&](int k) -> cplx* {
+            const Node& nd = c->nodes[k];
+            const int d0 = nd.d[0], d1 = nd.d[1], d2 = nd.d[2];
+            const long long s = nd.s, d12 = (long long)d1 * d2;
+            cplx* G0 = child_gram(nd, 0);
+            leg_apply(c, gam[k], d2, c->T[k], nd.d, 2, Wsc, 0.0, nb, (long long)d2 * d2, s);
+            project(c, c->T[k], nd.d, Wsc, nd.d, 0, G0, nb, s, (long long)d0 * d0);
+            c->stats[3] += k_trace_normalize(G0, d0, (long long)d0 * d0, nb, c->stream);
+            const cplx* w0 = walk_child(nd, 0);
+            GemmArgs g = base_args();   // Y_b = w0_b x_0 X: (d1 d2) x shots
+            g.M = (int)d12; g.N = nb; g.Ki = d0;
+            g.A = c->T[k]; g.a_m = d0; g.a_ki = 1;
+            g.B = w0; g.b_ki = 1; g.b_n = d0;
+            g.C = Y[k]; g.c_m = 1; g.c_n = d12;
+            gemm(c, g);
+            g = base_args();            // W1_b(c1', a) = sum_a' Y_b(c1', a') Gamma_b(a, a')
+            g.M = d1; g.N = d2; g.Ki = d2; g.Bi = nb;
+            g.A = Y[k]; g.a_m = 1; g.a_ki = d1; g.a_bi = d12;
+            g.B = gam[k]; g.b_ki = d2; g.b_n = 1; g.b_bi = (long long)d2 * d2;
+            g.C = Wsc; g.c_m = 1; g.c_n = d1; g.c_bi = d12;
+            gemm(c, g);
+            cplx* G1 = child_gram(nd, 1);
+            g = base_args();            // G1_b(c1, c1') = sum_a conj Y_b(c1, a) W1_b(c1', a)
+            g.M = d1; g.N = d1; g.Ki = d2; g.Bi = nb;
+            g.A = Y[k]; g.a_m = 1; g.a_ki = d1; g.a_bi = d12; g.conjA = 1;
+            g.B = Wsc; g.b_ki = d1; g.b_n = 1; g.b_bi = d12;
+            g.C = G1; g.c_m = 1; g.c_n = d1; g.c_bi = (long long)d1 * d1;
+            gemm(c, g);
+            c->stats[3] += k_trace_normalize(G1, d1, (long long)d1 * d1, nb, c->stream);
+            const cplx* w1 = walk_child(nd, 1);
+            g = base_args();            // w_b(a) = sum_c1 w1_b(c1) Y_b(c1, a)
+            g.M = d2; g.N = 1; g.Ki = d1; g.Bi = nb;
+            g.A = Y[k]; g.a_m = d1; g.a_ki = 1; g.a_bi = d12;
+            g.B = w1; g.b_ki = 1; g.b_n = d1; g.b_bi = d1;
+            g.C = wout[k]; g.c_m = 1; g.c_n = d2; g.c_bi = d2;
+            gemm(c, g);
+            c->stats[3] += k_vec_normalize(wout[k], d2, d2, nb, c->stream);
+            return wout[k];
+        };
+        for (int b0 = 0; b0 < n_shots; b0 += S) {
+            nb = std::min(S, n_shots - b0);
+            CUDA_OK(cudaMemcpyAsync(dU, uniforms + (size_t)b0 * N, sizeof(double) * (size_t)nb * N,
+                                    cudaMemcpyHostToDevice, c->stream));
+            c->stats[3] += k_fill(gam[c->root], nb, C(1.0), c->stream);   // root Gram [[1]] per shot
+            visit(c->root);
+            CUDA_OK(cudaMemcpyAsync(outcomes + (size_t)b0 * N, dO, sizeof(int) * (size_t)nb * N,
+                                    cudaMemcpyDeviceToHost, c->stream));
+            CUDA_OK(cudaStreamSynchronize(c->stream));
+        }
+        sync_check(c);
     });
 }
 

@@ -32,6 +32,8 @@ SIGNATURES = [
     ("ttn_set_hamiltonian", ctypes.c_int, [_P, _D, ctypes.c_double, ctypes.c_double]),
     ("ttn_apply_pulse", ctypes.c_int, [_P, _P, ctypes.c_int]),
     ("ttn_set_decay", ctypes.c_int, [_P, ctypes.c_double]),
+    ("ttn_compress", ctypes.c_int, [_P, _P, _D]),
+    ("ttn_sample", ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
     ("ttn_set_product_state", ctypes.c_int, [_P, _D]),
     ("ttn_set_ghz_target", ctypes.c_int, [_P, _I, ctypes.c_double]),
     ("ttn_tdvp_step", ctypes.c_int, [_P, ctypes.c_double]),
@@ -271,6 +273,25 @@ class TTN:
     # -- evolution and observables -------------------------------------------
     def step(self, dt):
         self._check(self.lib.ttn_tdvp_step(self.h, float(dt)), "tdvp_step")
+
+    def compress_into(self, dst):
+        """Truncate this state into dst (smaller bond dimension, same
+        lattice): returns (sum, max) of the discarded bond weights."""
+        out = np.zeros(2)
+        self._check(self.lib.ttn_compress(self.h, dst.h, _dptr(out)), "compress")
+        return float(out[0]), float(out[1])
+
+    def sample(self, uniforms):
+        """Projective measurement shots: uniforms (shots x N, column j = the
+        j-th real atom in leaf order) -> outcomes (shots x N ints, column =
+        atom id; 0: |0>, 1: |1>, 2: |r>)."""
+        U = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+        if U.ndim != 2 or U.shape[1] != self.N:
+            raise ValueError("uniforms must have shape (shots, %d)" % self.N)
+        out = np.zeros(U.shape, dtype=np.int32)
+        self._check(self.lib.ttn_sample(self.h, U.ctypes.data_as(_D), U.shape[0],
+                                        out.ctypes.data_as(_I)), "sample")
+        return out
 
     def overlap(self, target):
         out = np.zeros(2)
