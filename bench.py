@@ -130,8 +130,10 @@ def make_ctx(native, precision, stream):
     return g
 
 
-def time_steps(torch, g, stream, k, profile=False):
-    """K steps timed with CUDA events on the library's stream."""
+def time_steps(torch, g, stream, k, profile=False, tag="bench_step"):
+    """K steps timed with CUDA events on the library's stream, each step in an
+    NVTX range `tag` (the headline's steps in "bench_step", so that a
+    profiler can capture exactly those)."""
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if profile:
@@ -140,7 +142,7 @@ def time_steps(torch, g, stream, k, profile=False):
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(k):
-        torch.cuda.nvtx.range_push("bench_step")   # lets a profiler capture exactly the timed steps
+        torch.cuda.nvtx.range_push(tag)
         g.step(DT)
         torch.cuda.nvtx.range_pop()
     e1.record(stream)
@@ -313,8 +315,8 @@ def main():
     ap.add_argument("--full-rank-steps", type=int, default=2, help="timed steps from a full-rank start (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-out", default=None, help="write the kernel profile JSON here")
-    ap.add_argument("--lattice", default=None, help="LXxLY of a smaller case (profiling); default 8x8")
-    ap.add_argument("--chi", type=int, default=None, help="bond dimension of a smaller case; default 128")
+    ap.add_argument("--lattice", default=None, help="LXxLY of another case of the same recipe (profiling, chi=256); default 8x8")
+    ap.add_argument("--chi", type=int, default=None, help="bond dimension of another case; default 128")
     args = ap.parse_args()
     global LX, LY, CHI, WORKLOAD
     if args.lattice or args.chi:
@@ -322,7 +324,7 @@ def main():
             LX, LY = (int(v) for v in args.lattice.lower().split("x"))
         if args.chi:
             CHI = args.chi
-        WORKLOAD = "%dx%d Rydberg lattice, chi=%d (smaller case of the same workload recipe)" % (LX, LY, CHI)
+        WORKLOAD = "%dx%d Rydberg lattice, chi=%d (another case of the same workload recipe: same pulses, |+> start, dt)" % (LX, LY, CHI)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -359,7 +361,7 @@ def main():
     # second pass: the same steps with CUDA events around every contraction and
     # QR launch (kernel-class times for the roofline); not the headline
     n_prof = max(1, min(args.steps, args.profile_steps))
-    p_secs, _, prof = time_steps(torch, g, stream, n_prof, profile=True)
+    p_secs, _, prof = time_steps(torch, g, stream, n_prof, profile=True, tag="profile_step")
 
     # e2e through the public API with host buffers: schedule in, populations out
     from paper_2210_03763_gb300 import workloads as W
@@ -432,7 +434,7 @@ def main():
             h.set_node(k, X)
         h.refresh_envs()
         h.step(DT)
-        fr_secs, _, _ = time_steps(torch, h, stream, args.full_rank_steps, profile=False)
+        fr_secs, _, _ = time_steps(torch, h, stream, args.full_rank_steps, profile=False, tag="full_rank_step")
         result["full_rank_start"] = {"value": args.full_rank_steps / fr_secs, "unit": "steps/s",
                                      "steps": args.full_rank_steps}
         h.close()
@@ -442,7 +444,7 @@ def main():
         s2 = make_ctx(native, native.SPLIT_TF32X3, stream)
         f.step(DT)                      # warm-up step (also the first comparison step)
         s2.step(DT)
-        f_secs, f_stats, f_prof = time_steps(torch, f, stream, args.fp64_steps, profile=True)
+        f_secs, f_stats, f_prof = time_steps(torch, f, stream, args.fp64_steps, profile=True, tag="fp64_step")
         for _ in range(args.fp64_steps):
             s2.step(DT)
         ov = s2.overlap(f)

@@ -207,8 +207,12 @@ constexpr int QR_SC_MAXR = 64;   // structured completion when the kept rank r <
 // column-major) written.  cand[0..ncand) is the completion candidate order.
 // Returns the number of kernels launched, or -1 when a bounded device wait
 // of the cooperative column loop gave up (A and R are then undefined).
+// tol: a column is dependent when its residual is <= tol ||A||_F (the
+// dependence threshold of the completion rule, 1e-10 for every QR of the
+// library).
+constexpr double QR_TOL_FP64 = 1e-10;
 int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand,
-            QrScratch& ws, cudaStream_t s, int* n_dependent_host);
+            QrScratch& ws, cudaStream_t s, int* n_dependent_host, double tol = QR_TOL_FP64);
 
 // ---- truncated SVD (svd.cu) -----------------------------------------------------
 // One-sided Jacobi SVD of the N x N column-major R (N <= 256) in place: R's

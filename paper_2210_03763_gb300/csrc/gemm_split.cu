@@ -38,12 +38,8 @@
 
 namespace {
 
-constexpr int BM = SPLIT_BM, BN = SPLIT_BN, BK = SPLIT_BK;   // BK in fp32 elements = 128 bytes
-constexpr int STAGES = 4;
+constexpr int BM = SPLIT_BM, BK = SPLIT_BK;   // BK in fp32 elements = 128 bytes
 constexpr int A_TILE = BM * BK * 4;          // 16 KB per plane tile of P
-constexpr int B_TILE = BN * BK * 4;          // 8 KB per plane tile of Q
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr long long SPIN_LIMIT = 1LL << 30;                  // iteration cap behind the time limit
 constexpr unsigned long long WAIT_NS = 2000000000ull;        // 2 s per pipeline wait
 
@@ -127,15 +123,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 64.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = n.
+constexpr uint32_t idesc_for(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             dt),
-        "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -270,9 +267,41 @@ constexpr int CHUNK_KB = 2;
 constexpr int NBUF = 4;                            // TMEM accumulators (NBUF * BN columns)
 constexpr int DRAIN_WARPS = 16;                    // warp w: TMEM lanes 32 (w % 4) .., columns DCOLS (w / 4) ..
 constexpr int DRAIN_THREADS = 32 * DRAIN_WARPS;
-constexpr int DCOLS = BN / (DRAIN_WARPS / 4);      // columns per drain thread
 constexpr int TMA_WARP = DRAIN_WARPS, MMA_WARP = DRAIN_WARPS + 1;
 constexpr int GEMM_THREADS = DRAIN_THREADS + 64;
+
+// Tile width N of C~ (real columns, i.e. BN / 2 complex Q rows).  Both widths
+// use M = 128 rows and 4 TMEM accumulators (256 or all 512 columns).  The
+// wide tile halves the shared-memory operand traffic per flop (each 128-row P
+// tile feeds 128 columns instead of 64): measured on the H_eff of 8x8,
+// chi = 128 nodes, the tensor-core time of one matvec fell from 26.4 to
+// 18.4 ms over levels 2-4 (a copy of the kernel that skipped the drain and
+// the epilogue ran 21.1 ms at width 64 and 12.2 ms at width 128, so the
+// narrow tile was bound by its TMA/MMA pipeline, not by the drain).  Its
+// ring has 3 stages of 64 KB (4 of 48 KB at width 64), and each drain
+// thread holds 32 float-float sums.
+template <int BN_>
+struct TileCfg {
+    static constexpr int BN = BN_;
+    static constexpr int STAGES = BN_ == 128 ? 3 : 4;
+    static constexpr int B_TILE = BN_ * BK * 4;   // 8 or 16 KB per plane tile of Q
+    static constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr int DCOLS = BN_ / (DRAIN_WARPS / 4);   // columns per drain thread
+    static constexpr uint32_t IDESC = idesc_for(BN_);
+};
+static_assert(TileCfg<128>::SMEM_BYTES <= 227 * 1024 && TileCfg<64>::SMEM_BYTES <= 227 * 1024, "shared memory");
+static_assert(NBUF * 128 <= 512, "TMEM columns");
+
+// Tile width of a contraction: 128 when the Q side has at least 128 padded
+// real rows and the contraction is large (at least 2^24 complex MACs); small
+// contractions are latency-bound on a few CTAs and run faster as more,
+// narrower tiles (measured: 81 x 81 x 81 took 17 us at width 64, 24 us at
+// width 128).
+inline int tile_bn(int Qp, double cmacs) { return (Qp >= 128 && cmacs >= 16777216.0) ? 128 : 64; }
+inline int tile_bn(const SplitMma& m) {
+    return tile_bn(m.Qp, (double)m.Pn * m.Qn * (0.5 * m.Kp) * m.Bi * (double)m.Bo);
+}
 
 struct EpiArgs {
     cplx* C;
@@ -338,9 +367,13 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
     lo = __fadd_rn(lo, e);
 }
 
+template <int BN_>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
                    const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl, EpiArgs ea) {
+    using T = TileCfg<BN_>;
+    constexpr int BN = T::BN, STAGES = T::STAGES, B_TILE = T::B_TILE, STAGE_BYTES = T::STAGE_BYTES,
+                  DCOLS = T::DCOLS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -471,9 +504,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         for (int ks = 0; ks < BK / 8; ++ks) {
                             uint64_t off = (uint64_t)(ks * 32) >> 4;   // 8 tf32 = 32 bytes along K
                             uint32_t acc = (kb > c * CHUNK_KB || ks > 0) ? 1u : 0u;
-                            mma_tf32(dt, pl + off, qh + off, acc);
-                            mma_tf32(dt, ph + off, ql + off, 1u);
-                            mma_tf32(dt, ph + off, qh + off, 1u);
+                            mma_tf32(dt, pl + off, qh + off, T::IDESC, acc);
+                            mma_tf32(dt, ph + off, ql + off, T::IDESC, 1u);
+                            mma_tf32(dt, ph + off, qh + off, T::IDESC, 1u);
                         }
                         mma_commit(&empty[s]);
                     }
@@ -633,7 +666,7 @@ __global__ void splitk_reduce_kernel(EpiArgs ea) {
 constexpr int MAX_DEVICES = 64;
 struct DeviceState {
     int n_sm = 0;
-    bool attr_set = false;
+    bool attr_set[2] = {false, false};   // shared-memory attribute of the width-64 / width-128 kernels
 };
 DeviceState g_dev[MAX_DEVICES];
 std::mutex g_dev_mu;
@@ -726,7 +759,8 @@ SplitK choose_split(long long tiles, int nkb, int max_split) {
 }
 
 SplitK mma_split(const SplitMma& m) {
-    const long long tiles = (long long)(m.Pp / BM) * (m.Qp / BN) * m.Bi * (long long)m.Bo;
+    const int bn = tile_bn(m);
+    const long long tiles = (long long)(m.Pp / BM) * ((m.Qp + bn - 1) / bn) * m.Bi * (long long)m.Bo;
     return choose_split(tiles, m.Kp / BK, m.out ? 1 : m.max_split);
 }
 
@@ -762,9 +796,9 @@ Plan plan_for(const GemmArgs& g, int max_split) {
     pl.swapped = cost_b_p < cost_a_p || (cost_b_p == cost_a_p && g.N > g.M);
     const int Rp_rows = pl.swapped ? g.N : g.M, Rq_rows = pl.swapped ? g.M : g.N;
     pl.Pp = (int)round_up(Rp_rows, BM);
-    pl.Qp = (int)round_up(2LL * Rq_rows, BN);
+    pl.Qp = (int)round_up(2LL * Rq_rows, SPLIT_BN);
     pl.Kp = (int)round_up(2 * K, BK);
-    if (pl.batches > 65535 || pl.Qp / BN > 65535) return pl;
+    if (pl.batches > 65535 || pl.Qp / SPLIT_BN > 65535) return pl;
     pl.p_vbi = pl.swapped ? b_vbi : a_vbi;
     pl.p_vbo = pl.swapped ? b_vbo : a_vbo;
     pl.q_vbi = pl.swapped ? a_vbi : b_vbi;
@@ -855,20 +889,29 @@ size_t split_mma_partials(const SplitMma& m) {
 
 int split_mma(const SplitMma& m, int* err_flag, void* partials, size_t partial_bytes, cudaStream_t stream) {
     if (!err_flag || partial_bytes < split_mma_partials(m) || (split_mma_partials(m) > 0 && !partials)) return -2;
-    if (m.Kp % BK || m.Pp % BM || m.Qp % BN || m.Bi < 1 || m.Bo < 1 || m.Pn < 1 || m.Qn < 1) return -1;
+    if (m.Kp % BK || m.Pp % BM || m.Qp % SPLIT_BN || m.Bi < 1 || m.Bo < 1 || m.Pn < 1 || m.Qn < 1) return -1;
+    const int bn = tile_bn(m);
+    const int smem_bytes = bn == 128 ? TileCfg<128>::SMEM_BYTES : TileCfg<64>::SMEM_BYTES;
     {
         DeviceState& d = device_state();
         std::lock_guard<std::mutex> lock(g_dev_mu);
-        if (!d.attr_set) {
-            if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-                cudaSuccess)
-                return -1;
-            d.attr_set = true;
+        const int w = bn == 128 ? 1 : 0;
+        if (!d.attr_set[w]) {
+            const cudaError_t e =
+                bn == 128 ? cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 smem_bytes)
+                          : cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 smem_bytes);
+            if (e != cudaSuccess) return -1;
+            d.attr_set[w] = true;
         }
     }
+    // Q maps: boxes of bn rows; a wide tile that runs past a batch's Qp rows
+    // reads the next batch's rows or, past the end, TMA's zero fill, and the
+    // epilogue drops those columns (q >= Qn)
     CUtensorMap mPh, mPl, mQh, mQl;
     if (!make_map(&mPh, m.Ph, m.P_rows, m.Kp, m.P_pitch, BM) || !make_map(&mPl, m.Pl, m.P_rows, m.Kp, m.P_pitch, BM) ||
-        !make_map(&mQh, m.Qh, m.Q_rows, m.Kp, m.Q_pitch, BN) || !make_map(&mQl, m.Ql, m.Q_rows, m.Kp, m.Q_pitch, BN))
+        !make_map(&mQh, m.Qh, m.Q_rows, m.Kp, m.Q_pitch, bn) || !make_map(&mQl, m.Ql, m.Q_rows, m.Kp, m.Q_pitch, bn))
         return -1;
     const SplitK sk = mma_split(m);
     EpiArgs ea;
@@ -897,12 +940,15 @@ int split_mma(const SplitMma& m, int* err_flag, void* partials, size_t partial_b
     // fastest so that CTAs sharing the other operand's tile run together and
     // hit it in L2 (an operand larger than L2 is then read about once)
     ea.n_ptiles = m.Pp / BM;
-    ea.n_qtiles = m.Qp / BN;
+    ea.n_qtiles = (m.Qp + bn - 1) / bn;
     ea.q_fast = ea.n_qtiles < ea.n_ptiles;
     ea.batches = m.Bi * m.Bo;
     const long long ntiles = (long long)ea.n_ptiles * ea.n_qtiles * ea.batches * sk.nsplit;
     const unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms());
-    tc_gemm_kernel<<<grid, GEMM_THREADS, SMEM_BYTES, stream>>>(mPh, mPl, mQh, mQl, ea);
+    if (bn == 128)
+        tc_gemm_kernel<128><<<grid, GEMM_THREADS, smem_bytes, stream>>>(mPh, mPl, mQh, mQl, ea);
+    else
+        tc_gemm_kernel<64><<<grid, GEMM_THREADS, smem_bytes, stream>>>(mPh, mPl, mQh, mQl, ea);
     if (sk.nsplit == 1) return 1;
     const long long total = (long long)m.Pn * m.Qn * ea.batches;
     const unsigned rg = (unsigned)std::min<long long>((total + 255) / 256, (long long)num_sms() * 8);

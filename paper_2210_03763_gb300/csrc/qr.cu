@@ -3,7 +3,8 @@
 //
 // Column-by-column classical Gram-Schmidt with one re-orthogonalisation pass
 // (CGS2), in place on a column-major M x D matrix.  Column k is *dependent*
-// when the norm of its residual after both passes is <= 1e-10 ||A||_F; it is
+// when the norm of its residual after both passes is <= tol ||A||_F (1e-10
+// unless the caller passes another threshold); it is
 // zeroed (R_kk = 0) and filled after the sweep, in increasing k, by the first
 // candidate unit vector e_c (in the caller's candidate order) whose residual
 // 1 - ||Q^H e_c||^2 is >= 1/4 (else the candidate with the largest residual,
@@ -36,7 +37,6 @@
 
 namespace {
 
-constexpr double QR_TOL = 1e-10;
 constexpr double MIN_RES2 = 0.25;
 constexpr int QB = QR_ROWS;      // rows per block = threads per block
 constexpr int MAXD = 256;        // maximal bond dimension
@@ -124,10 +124,11 @@ __global__ void __launch_bounds__(QB) col_norm_kernel(const cplx* A, long long M
 
 // Decide column kd from its norm partials: R_kk, flag, factor (identical in
 // every block; block 0 stores them).
-__device__ double decide(int kd, const double* pnorm, int G, double* scal, cplx* R, int D, int* flags) {
+__device__ double decide(int kd, const double* pnorm, int G, double* scal, cplx* R, int D, int* flags,
+                         double tol) {
     double s = sum_norm(pnorm, G);
     double nrm = sqrt(s), fro = sqrt(scal[0]);
-    int dep = (fro == 0.0) || (nrm <= QR_TOL * fro);
+    int dep = (fro == 0.0) || (nrm <= tol * fro);
     if (blockIdx.x == 0) {
         R[(long long)kd * D + kd] = make_double2(dep ? 0.0 : nrm, 0.0);
         scal[1] = dep ? 0.0 : 1.0 / nrm;
@@ -147,8 +148,8 @@ struct PhaseSmem {
 
 // K1 for column k >= 1: decide column k-1, dots of a_k with columns < k
 __device__ void phase_k1(const cplx* A, long long M, int D, int k, const double* pnorm, int G, double* scal, cplx* R,
-                         int* flags, cplx* part, PhaseSmem& sm) {
-    if (threadIdx.x == 0) sm.sfac = decide(k - 1, pnorm, G, scal, R, D, flags);
+                         int* flags, cplx* part, double tol, PhaseSmem& sm) {
+    if (threadIdx.x == 0) sm.sfac = decide(k - 1, pnorm, G, scal, R, D, flags, tol);
     for (int i = threadIdx.x; i < k - 1; i += QB) sm.szero[i] = flags[i];
     __syncthreads();
     if (threadIdx.x == 0) sm.szero[k - 1] = (sm.sfac == 0.0);
@@ -220,9 +221,9 @@ __device__ void phase_k3(cplx* A, long long M, int D, int k, const int* flags, c
 }
 
 __global__ void __launch_bounds__(QB) qr_k1(const cplx* A, long long M, int D, int k, const double* pnorm, int G,
-                                            double* scal, cplx* R, int* flags, cplx* part) {
+                                            double* scal, cplx* R, int* flags, cplx* part, double tol) {
     __shared__ PhaseSmem sm;
-    phase_k1(A, M, D, k, pnorm, G, scal, R, flags, part, sm);
+    phase_k1(A, M, D, k, pnorm, G, scal, R, flags, part, tol, sm);
 }
 
 __global__ void __launch_bounds__(QB) qr_k2(cplx* A, long long M, int D, int k, const int* flags, const double* scal,
@@ -604,7 +605,7 @@ __device__ void la_dots(int P, PairF pair, cplx* out, const cplx* A, long long M
 }
 
 __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D, cplx* R, int* flags, cplx* part,
-                                                     cplx* red_out, unsigned* bar, int* err, int nc_max) {
+                                                     cplx* red_out, unsigned* bar, int* err, int nc_max, double tol) {
     // dynamic shared memory: nc_max cached columns of QCS rows, then the
     // look-ahead window (this block's rows of v1_j)
     extern __shared__ cplx dyn[];
@@ -659,7 +660,7 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
             block_sum3(s2, px, py, sm);
             if (t == 0) {
                 const double nrm = sqrt(fmax(sm.hb[2 * n + 1].x - s2, 0.0)), f = sqrt(sm.fro2);
-                const int dep = (f == 0.0) || (nrm <= QR_TOL * f);
+                const int dep = (f == 0.0) || (nrm <= tol * f);
                 const double sc = dep ? 0.0 : 1.0 / nrm;
                 sm.dep = dep;
                 sm.scale = sc;
@@ -760,7 +761,7 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
                 double nrm = 0.0;
                 for (int j = 0; j < W; ++j) {
                     nrm = sqrt(fmax(sm.hb[o_nv + j].x - la_s2[j], 0.0));
-                    const int dep = (f == 0.0) || (nrm <= QR_TOL * f);
+                    const int dep = (f == 0.0) || (nrm <= tol * f);
                     if (b0) {
                         R[(long long)(k0 + j) * D + (k0 + j)] = make_double2(dep ? 0.0 : nrm, 0.0);
                         flags[k0 + j] = dep;
@@ -843,9 +844,9 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
 
 // Decide and scale the last column.
 __global__ void __launch_bounds__(QB) qr_last(cplx* A, long long M, int D, const double* pnorm, int G, double* scal,
-                                              cplx* R, int* flags) {
+                                              cplx* R, int* flags, double tol) {
     __shared__ double sfac;
-    if (threadIdx.x == 0) sfac = decide(D - 1, pnorm, G, scal, R, D, flags);
+    if (threadIdx.x == 0) sfac = decide(D - 1, pnorm, G, scal, R, D, flags, tol);
     __syncthreads();
     long long r = blockIdx.x * (long long)QB + threadIdx.x;
     if (r < M) {
@@ -1160,7 +1161,7 @@ __global__ void __launch_bounds__(QB) sc_materialize_kernel(cplx* A, long long M
 }  // namespace
 
 int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratch& ws, cudaStream_t s,
-            int* n_dependent_host) {
+            int* n_dependent_host, double tol) {
     int launches = 0;
     const long long MM = M;
     const int G = (int)((MM + QB - 1) / QB);
@@ -1194,7 +1195,7 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
         // the barrier leaves its arrival count at zero after every completed
         // wait, so it needs a reset only after an error
         void* args[] = {(void*)&A, (void*)&MM, (void*)&D, (void*)&R, (void*)&ws.flags, (void*)&ws.part,
-                        (void*)&ws.h, (void*)&ws.bar, (void*)&ws.err, (void*)&nc};
+                        (void*)&ws.h, (void*)&ws.bar, (void*)&ws.err, (void*)&nc, (void*)&tol};
         coop_done = cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(G), dim3(QB), args, smem, s) ==
                     cudaSuccess;
         if (!coop_done) cudaGetLastError();   // clear and use the multi-launch path
@@ -1207,12 +1208,12 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
         col_norm_kernel<<<G, QB, 0, s>>>(A, MM, ws.pnorm);
         launches += 3;
         for (int k = 1; k < D; ++k) {
-            qr_k1<<<G, QB, 0, s>>>(A, MM, D, k, ws.pnorm, G, ws.scal, R, ws.flags, part1);
+            qr_k1<<<G, QB, 0, s>>>(A, MM, D, k, ws.pnorm, G, ws.scal, R, ws.flags, part1, tol);
             qr_k2<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, ws.scal, part1, part2, R, G);
             qr_k3<<<G, QB, 0, s>>>(A, MM, D, k, ws.flags, part2, R, ws.pnorm, G);
             launches += 3;
         }
-        qr_last<<<G, QB, 0, s>>>(A, MM, D, ws.pnorm, G, ws.scal, R, ws.flags);
+        qr_last<<<G, QB, 0, s>>>(A, MM, D, ws.pnorm, G, ws.scal, R, ws.flags, tol);
         launches += 1;
     }
 

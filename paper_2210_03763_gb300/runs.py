@@ -20,6 +20,10 @@ benchmark (each prints one JSON line; every input is seeded and synthetic):
         interaction between codes); the crosstalk infidelity is
         1 - |<isolated|full>|^2 / (norms) after `steps` steps, with the
         split-precision steps/s.
+    python -m paper_2210_03763_gb300.runs sample Lx Ly chi shots
+        projective measurement shots per second (ttn_sample, FP64 and split
+        precision) on the state after 3 steps of the CZ-layer workload from
+        |+>^N, and the fraction of shots both precisions draw alike.
 """
 import json
 import math
@@ -145,8 +149,36 @@ def repcode(chi, steps, dt=0.05):
     return res
 
 
+def sample(Lx, Ly, chi, shots, steps=3, dt=0.01):
+    """Shots/s of the projective measurement walk (ttn_sample) on the state
+    after `steps` split-precision steps of the CZ-layer workload from |+>^N,
+    in FP64 and in split precision, with the fraction of shots on which the
+    two precisions draw the same outcomes from the same uniforms."""
+    N = Lx * Ly
+    xy = W.square_lattice(Lx, Ly)
+    r_G = 4.0 if (Lx, Ly) == (8, 8) else math.sqrt(8.0)
+    sched, _ = W.cz_layer_workload(Lx, Ly, r_G)
+    g = _ctx(Lx, Ly, chi, native.SPLIT_TF32X3, xy, 20.0, sched, W.plus_state_amps(N))
+    for _ in range(steps):
+        g.step(dt)
+    U = np.random.default_rng(7).random((shots, N))
+    out = {"run": "sample", "lattice": "%dx%d" % (Lx, Ly), "chi": chi, "shots": shots, "steps_before": steps}
+    res = {}
+    for name, prec in (("fp64", native.FP64), ("split", native.SPLIT_TF32X3)):
+        g.set_precision(prec)
+        g.sample(U[:2])          # warm-up: workspaces
+        t0 = _sync_time()
+        res[name] = g.sample(U)
+        t1 = _sync_time()
+        out[name + "_shots_per_s"] = shots / (t1 - t0)
+    out["same_outcomes"] = float(np.mean(np.all(res["fp64"] == res["split"], axis=1)))
+    out["mean_rydberg_per_shot"] = float(np.mean(np.sum(res["fp64"] == 2, axis=1)))
+    g.close()
+    return out
+
+
 def main(argv):
-    if not argv or argv[0] not in ("window", "repcode"):
+    if not argv or argv[0] not in ("window", "repcode", "sample"):
         print(__doc__)
         return 2
     native.load()
@@ -155,6 +187,9 @@ def main(argv):
         dt = float(argv[5]) if len(argv) > 5 else 0.01
         r_G = float(argv[6]) if len(argv) > 6 else None
         print(json.dumps(window(Lx, Ly, chi, steps, dt, r_G)))
+    elif argv[0] == "sample":
+        Lx, Ly, chi, shots = (int(v) for v in argv[1:5])
+        print(json.dumps(sample(Lx, Ly, chi, shots)))
     else:
         chi, steps = int(argv[1]), int(argv[2])
         dt = float(argv[3]) if len(argv) > 3 else 0.05

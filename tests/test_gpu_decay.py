@@ -12,7 +12,15 @@ instead of Lanczos) against the CPU oracle:
   d<psi|psi>/dt = 2 Im <psi|H|psi> = -2 gamma sum <n> because the projected
   generator acts on psi as H does), to the O(dt^2) of the integrator and of
   the trapezoid rule (relative 1e-3 at dt = 0.01);
-* split precision with decay tracks the FP64 run (norm 1e-8).
+* split precision with decay tracks the FP64 run from a full-rank random
+  start (4x4, chi = 64, 5 steps): state infidelity 1e-9 and norm 5e-6
+  (measured 1.2e-10 and 5.7e-7).  Looser than the closed system's norm
+  because Arnoldi, unlike Lanczos, does not symmetrise the projected
+  generator, so the anti-Hermitian part of the split contraction error moves
+  the norm.  A product-state start is not used: its rank-deficient bonds are
+  completed from residuals near the dependence threshold (reading A10), so
+  two precisions can complete differently and then follow different, equally
+  valid projected dynamics (measured 2e-6 infidelity without decay as well).
 """
 import numpy as np
 import pytest
@@ -118,13 +126,18 @@ def test_split_decay_tracks_fp64(native):
         g.set_hamiltonian(xy, 20.0)
         g.apply_pulse(sched)
         g.set_decay(GAMMA)
-        g.set_product_state(W.random_product_amps(16, 9))
+        shapes = [g.node_info(k)[0] for k in range(g.num_nodes())]
+        for k, X in enumerate(W.random_ttn_tensors(shapes, 41)):
+            g.set_node(k, X)
+        g.refresh_envs()
         for _ in range(5):
             g.step(0.02)
         runs.append(g)
     a, b = runs
-    assert abs(a.norm() - b.norm()) < 1e-8
+    dn = abs(a.norm() - b.norm())
     infid = 1 - abs(a.overlap(b)) ** 2 / (a.norm() * b.norm())
-    assert infid < 1e-10
+    assert 1 - b.norm() > 1e-3          # the decay acted
+    assert dn < 5e-6, dn
+    assert infid < 1e-9, infid
     a.close()
     b.close()

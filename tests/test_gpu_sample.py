@@ -96,8 +96,8 @@ def test_full_size_frequencies_and_split_agreement(native):
         g.set_hamiltonian(xy, 20.0)
         g.apply_pulse(sched)
         g.set_product_state(W.random_product_amps(N, 22))
-        for _ in range(2):
-            g.step(0.1)
+        for _ in range(3):
+            g.step(0.02)
         g.set_precision(prec)
         runs.append(g)
     f, s = runs

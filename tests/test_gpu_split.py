@@ -196,3 +196,41 @@ def test_split_steps_preserve_the_norm(native):
         g.step(0.02)
     assert abs(g.norm() - n0) < NORM_TOL * n0, g.norm() - n0
     g.close()
+
+
+def test_split_tracks_fp64_from_a_product_state(native):
+    # A product start with |r> populated has rank-deficient bonds.  In the
+    # first step TDVP grows new bond directions from them; the split run's
+    # node tensors carry ~5e-7 relative noise in the still-empty directions,
+    # the QR keeps those columns (their residual is above the 1e-10
+    # dependence threshold of reading A10) where the FP64 run completes them
+    # by the deterministic rule, so the two runs project on different
+    # tangent spaces from then on.  Measured: 1.9e-6 infidelity after one
+    # step of 0.02, not growing over the next four (1.9e-6 after 5).  (A
+    # split-only threshold of 1e-5 made it 2e-5: it also replaced real
+    # directions still below 1e-5 by completion vectors.)  From |+>^N, whose
+    # bonds grow symmetrically, the two precisions agree to 4e-12 over a
+    # whole CZ layer, and from full-rank starts to 1e-10.
+    Lx = Ly = 4
+    xy = W.square_lattice(Lx, Ly)
+    sched, _ = W.cz_layer_workload(Lx, Ly, 2.0 ** 1.5)
+    runs = []
+    for prec in (native.SPLIT_TF32X3, native.FP64):
+        g = native.TTN(Lx, Ly, 64)
+        g.set_precision(prec)
+        g.set_hamiltonian(xy, 20.0)
+        g.apply_pulse(sched)
+        g.set_product_state(W.random_product_amps(16, 9))
+        g.step(0.02)
+        runs.append(g)
+    a, b = runs
+    first = 1 - abs(a.overlap(b)) ** 2 / (a.norm() * b.norm())
+    for _ in range(4):
+        a.step(0.02)
+        b.step(0.02)
+    later = 1 - abs(a.overlap(b)) ** 2 / (a.norm() * b.norm())
+    assert first < 5e-6, first
+    assert later < 2 * first + 1e-9, (first, later)
+    assert abs(a.norm() - b.norm()) < 1e-9
+    a.close()
+    b.close()
