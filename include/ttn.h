@@ -185,6 +185,38 @@ ttn_status ttn_compress(ttn_ctx* src, ttn_ctx* dst, double* discarded);
  * buffers -> TTN_ERR_ARG; allocation failure -> TTN_ERR_ALLOC. */
 ttn_status ttn_sample(ttn_ctx* ctx, const double* uniforms, int n_shots, int* outcomes);
 
+/* Gradient of the final-state fidelity F = |<target|psi(t0 + n_steps dt)>|^2
+ * with respect to piecewise-constant pulse parameters (the differentiation
+ * extension: pulse amplitudes Omega_k and detunings Delta_k of schedule rows
+ * of ttn_apply_pulse), starting from the context's current state at its
+ * current time t0.  Parameter p is field fields[p] (0: omega_r, the |r><1|
+ * coupling with dH = e^{i phase_r}|r><1| + h.c. on the row's atom; 1: delta,
+ * dH = -|r><r|) of schedule row rows[p].
+ * Method (adjoint of the time-stepping map): with U_n the n-th step and
+ * chi_n = U_{n+1}^H ... U_N^H |target>,
+ *   dF/dtheta = 2 Re( conj(A) sum_n <chi_n| dU_n/dtheta |psi_{n-1}> ),
+ *   <chi_n| dU_n |psi_{n-1}> = -i int_0^dt <chi(s)| dH |psi(s)> ds,
+ * psi(s) = e^{-isH} psi_{n-1}, chi(s) = e^{+i(dt-s)H} chi_n, the integral by
+ * n_quad-point Gauss-Legendre (1..8) on TDVP sub-steps of the same step
+ * Hamiltonian, the matrix elements from transition reduced density matrices
+ * of every atom (overlap environments of the two trees, FP64).  chi is
+ * propagated backwards by TDVP steps of -dt; psi is recomputed from
+ * checkpoints taken every `checkpoint_every` steps (<= 0: about
+ * sqrt(n_steps)), so device memory grows with n_steps / checkpoint_every
+ * copies of the state.  Where the bonds are complete (every TDVP projector
+ * is the identity) this is the gradient of the exact discrete map up to the
+ * quadrature error; in the truncated regime it is the adjoint of the
+ * projected dynamics, not the derivative of the discrete TDVP map (which
+ * also varies through the gauge and the projectors).
+ *   target : same lattice and bond dimension, centre at its root;
+ *   F, grad: host, 1 and n_params doubles.
+ * The context's state and time are restored on return.  No decay (gamma must
+ * be 0), n_steps >= 1, dt > 0, rows inside the schedule, fields 0 or 1,
+ * 1 <= n_quad <= 8, else TTN_ERR_ARG. */
+ttn_status ttn_fidelity_gradient(ttn_ctx* ctx, const ttn_ctx* target, double dt, int n_steps, int n_params,
+                                 const int* rows, const int* fields, int n_quad, int checkpoint_every,
+                                 double* F, double* grad);
+
 /* ---- introspection used by tests and tools ------------------------------ */
 ttn_status ttn_num_nodes(const ttn_ctx* ctx, int* n);
 /* dims[3] = (d0, d1, d2); children[2] = child node ids, or -(leaf+1) for a leaf. */
@@ -214,12 +246,15 @@ ttn_status ttn_apply_heff(ttn_ctx* ctx, int node, const double* x, double* y);
 ttn_status ttn_get_stats(const ttn_ctx* ctx, int64_t* out6);
 
 /* Kernel-level timing with CUDA events recorded on the context's stream.
- * Between begin and end every contraction launch (and every QR) is bracketed
- * by an event pair.  ttn_profile_end synchronises and fills out[16] with, for
- * kind k = 0 tensor-core GEMM (tcgen05), 1 split-operand packing, 2 FP64
- * GEMM, 3 QR: out[4k + 0] launches, [4k + 1] summed device time in ms,
- * [4k + 2] algorithmic flops (8 M N K per complex contraction; 16 M D^2 per
- * QR), [4k + 3] algorithmic bytes.  n must be >= 16. */
+ * Between begin and end every contraction launch, every QR and every group of
+ * Krylov vector kernels is bracketed by an event pair.  ttn_profile_end
+ * synchronises and fills out[4 * min(5, n / 4)] with, for kind k = 0
+ * tensor-core GEMM (tcgen05), 1 split-operand packing, 2 FP64 GEMM, 3 QR,
+ * 4 Krylov vector work (re-orthogonalisation, scalars, combination, one-block
+ * runs of small nodes): out[4k + 0] event pairs, [4k + 1] summed device time
+ * in ms, [4k + 2] algorithmic flops (8 M N K per complex contraction;
+ * 16 M D^2 per QR), [4k + 3] algorithmic bytes.  n must be >= 16 (kinds that
+ * do not fit are left out). */
 ttn_status ttn_profile_begin(ttn_ctx* ctx);
 /* Self-test of one contraction kernel, no context needed: seeded random
  * complex A (M x K) and B (K x N) with entries uniform in [-1, 1)^2

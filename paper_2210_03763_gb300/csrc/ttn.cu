@@ -246,8 +246,10 @@ void grow_split_ws(ttn_ctx* c, size_t bytes) {
     c->split_cap = cap;
 }
 
-// Profile kinds: 0 tensor-core GEMM, 1 split packing, 2 FP64 GEMM, 3 QR.
-enum { PK_TC = 0, PK_PACK = 1, PK_F64 = 2, PK_QR = 3, PK_N = 4 };
+// Profile kinds: 0 tensor-core GEMM, 1 split packing, 2 FP64 GEMM, 3 QR,
+// 4 Krylov vector work (re-orthogonalisation, scalars, combination, and the
+// one-block Krylov runs of small nodes).
+enum { PK_TC = 0, PK_PACK = 1, PK_F64 = 2, PK_QR = 3, PK_KRY = 4, PK_N = 5 };
 
 cudaEvent_t next_event(ttn_ctx* c) {
     if (c->ev_next == c->ev_pool.size()) {
@@ -911,23 +913,30 @@ void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
     const int mmax = test_krylov_mmax();
     cplx* V = c->Kbasis;
     const long long ld = n;
-    c->stats[3] += k_norm2_partial(x, n, c->kpn, s);
-    c->stats[3] += k_krylov_start_ex(c->ks, c->kpn, n, s);
-    c->stats[3] += k_scale_copy_dev(x, n, &c->ks->inv_scale, V, s);
+    {
+        ProfScope ps(c, PK_KRY, 0.0, 48.0 * n);
+        c->stats[3] += k_norm2_partial(x, n, c->kpn, s);
+        c->stats[3] += k_krylov_start_ex(c->ks, c->kpn, n, s);
+        c->stats[3] += k_scale_copy_dev(x, n, &c->ks->inv_scale, V, s);
+    }
     int j = 0;
     for (;; ++j) {
         cplx* vj = V + (long long)j * ld;
         cplx* w = V + (long long)(j + 1) * ld;
         apply(vj, w);
         c->stats[1] += 1;
-        c->stats[3] += k_dots_scaled(V, ld, j + 1, w, n, c->kpart, -1, nullptr, -1, s);
-        cplx* part2 = c->kpart + (size_t)RED_BLOCKS * (KRYLOV_MMAX + 1);
-        c->stats[3] += k_orth_update_ex(V, ld, j + 1, c->kpart, w, n, 1, part2, nullptr, c->kh1, 0, -1, s);
-        c->stats[3] += k_orth_update_ex(V, ld, j + 1, part2, w, n, 2, nullptr, c->kpn, c->kh2, 0, -1, s);
-        if (c->gamma != 0.0)   // non-Hermitian generator (decay): Arnoldi
-            c->stats[3] += k_arnoldi_scalars(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
-        else
-            c->stats[3] += k_krylov_scalars_ex(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
+        {
+            // bytes: the basis is read three times (dots, two update passes), w read and written twice
+            ProfScope ps(c, PK_KRY, 0.0, 16.0 * n * (3.0 * (j + 1) + 5.0));
+            c->stats[3] += k_dots_scaled(V, ld, j + 1, w, n, c->kpart, -1, nullptr, -1, s);
+            cplx* part2 = c->kpart + (size_t)RED_BLOCKS * (KRYLOV_MMAX + 1);
+            c->stats[3] += k_orth_update_ex(V, ld, j + 1, c->kpart, w, n, 1, part2, nullptr, c->kh1, 0, -1, s);
+            c->stats[3] += k_orth_update_ex(V, ld, j + 1, part2, w, n, 2, nullptr, c->kpn, c->kh2, 0, -1, s);
+            if (c->gamma != 0.0)   // non-Hermitian generator (decay): Arnoldi
+                c->stats[3] += k_arnoldi_scalars(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
+            else
+                c->stats[3] += k_krylov_scalars_ex(c->ks, c->kh1, c->kh2, c->kpn, n, j, zr, zi, tol, s);
+        }
         CUDA_OK(cudaMemcpyAsync(c->hflag, &c->ks->converged, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         c->hflag[2] = 0;
         if (c->split_ws)   // a tensor-core wait that gave up leaves garbage: report it first
@@ -936,6 +945,7 @@ void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
         if (c->hflag[2]) check_split_flag(c);
         if (c->hflag[1]) throw TtnError(TTN_ERR_NUMERIC, "non-finite value in Lanczos");
         if (c->hflag[0] || j == mmax - 1) break;
+        ProfScope ps(c, PK_KRY, 0.0, 32.0 * n);
         c->stats[3] += k_scale_copy_dev(w, n, &c->ks->inv_scale, w, s);
     }
     if (!c->hflag[0]) {
@@ -945,6 +955,7 @@ void krylov(ttn_ctx* c, cplx* x, long long n, double zr, double zi, F apply) {
         if (err > 1e-6) throw TtnError(TTN_ERR_KRYLOV, "Lanczos did not converge in m_max steps");
     }
     c->stats[0] += 1;
+    ProfScope ps(c, PK_KRY, 0.0, 16.0 * n * (j + 2));
     c->stats[3] += k_combine(V, ld, j + 1, c->ks, x, n, s);
 }
 
@@ -967,9 +978,12 @@ bool small_evolve(ttn_ctx* c, const int* d, cplx* const* hb, const Pair* pairs, 
         pp.G[p] = pairs[p].G;
     }
     const double tol = (c->prec == TTN_FP64) ? 1e-13 : 1e-9;
-    c->stats[3] += k_dense_heff(c->dense_H, d, hb[0], hb[1], hb[2], pp, c->stream);
-    c->stats[3] += k_small_krylov(c->dense_H, (int)s, x, zr, zi, tol, test_krylov_mmax(), c->gamma != 0.0 ? 1 : 0,
-                                  c->ks, c->stream);
+    {
+        ProfScope ps(c, PK_KRY, 0.0, 0.0);
+        c->stats[3] += k_dense_heff(c->dense_H, d, hb[0], hb[1], hb[2], pp, c->stream);
+        c->stats[3] += k_small_krylov(c->dense_H, (int)s, x, zr, zi, tol, test_krylov_mmax(),
+                                      c->gamma != 0.0 ? 1 : 0, c->ks, c->stream);
+    }
     struct {
         double alpha0;
         double err;
@@ -2289,17 +2303,19 @@ ttn_status ttn_profile_begin(ttn_ctx* c) {
 }
 
 ttn_status ttn_profile_end(ttn_ctx* c, double* out, int n) {
-    if (!c || !out || n < 4 * PK_N) return TTN_ERR_ARG;
+    if (!c || !out || n < 16) return TTN_ERR_ARG;
+    const int nk = std::min((int)PK_N, n / 4);   // kinds that fit in out
     return guard(c, [&] {
         c->profiling = false;
         CUDA_OK(cudaStreamSynchronize(c->stream));
-        for (int i = 0; i < 4 * PK_N; ++i) out[i] = 0.0;
+        for (int i = 0; i < 4 * nk; ++i) out[i] = 0.0;
         c->prof_last.clear();
         for (auto& r : c->prof) {
             float ms = 0.f;
             CUDA_OK(cudaEventElapsedTime(&ms, r.e0, r.e1));
             c->prof_last.push_back({(double)r.kind, (double)r.shape[0], (double)r.shape[1], (double)r.shape[2],
                                     (double)r.shape[3], (double)ms, r.flops});
+            if (r.kind >= nk) continue;
             out[4 * r.kind + 0] += 1.0;
             out[4 * r.kind + 1] += ms;
             out[4 * r.kind + 2] += r.flops;
@@ -2826,6 +2842,310 @@ ttn_status ttn_sample(ttn_ctx* c, const double* uniforms, int n_shots, int* outc
             CUDA_OK(cudaStreamSynchronize(c->stream));
         }
         sync_check(c);
+    });
+}
+
+// ---------------------------------------------------------------- gradient
+namespace {
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on the
+// Legendre polynomial P_q from the Chebyshev guesses; three-term recurrence).
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(q, 0.0);
+    w.assign(q, 0.0);
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (q + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int n = 2; n <= q; ++n) {
+                const double p2 = ((2.0 * n - 1.0) * z * p1 - (n - 1.0) * p0) / n;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (q == 1) p0 = 1.0;
+            dp = q * (z * p1 - p0) / (z * z - 1.0);   // P_q'(z)
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Device copies of every node tensor of a context (a checkpoint).
+struct StateCopy {
+    std::vector<cplx*> T;
+    double t = 0.0;
+};
+
+void save_state(ttn_ctx* c, StateCopy& s, std::vector<void*>& temp) {
+    if (s.T.empty()) {
+        s.T.resize(c->nodes.size());
+        for (size_t k = 0; k < c->nodes.size(); ++k) {
+            void* p = nullptr;
+            if (test_take_alloc_fail() || cudaMalloc(&p, sizeof(cplx) * c->nodes[k].s) != cudaSuccess)
+                throw TtnError(TTN_ERR_ALLOC, "gradient checkpoints");
+            temp.push_back(p);
+            s.T[k] = (cplx*)p;
+        }
+    }
+    centre_to_root(c);
+    for (size_t k = 0; k < c->nodes.size(); ++k)
+        CUDA_OK(cudaMemcpyAsync(s.T[k], c->T[k], sizeof(cplx) * c->nodes[k].s, cudaMemcpyDeviceToDevice,
+                                c->stream));
+    s.t = c->t;
+}
+
+// Load a saved state (canonical, centre at the root) and rebuild the upward
+// environments.
+void load_state(ttn_ctx* c, const StateCopy& s) {
+    for (size_t k = 0; k < c->nodes.size(); ++k)
+        CUDA_OK(cudaMemcpyAsync(c->T[k], s.T[k], sizeof(cplx) * c->nodes[k].s, cudaMemcpyDeviceToDevice,
+                                c->stream));
+    c->centre = c->root;
+    c->t = s.t;
+    rebuild_up_envs(c);
+}
+
+// One TDVP step of signed length h with the Hamiltonian at time tm (the
+// midpoint of the step being differentiated).
+void step_at(ttn_ctx* c, double tm, double h) {
+    centre_to_root(c);
+    compute_coef(c, tm);
+    sweep_fwd(c, c->root, 0.5 * h);
+    sweep_rev(c, c->root, 0.5 * h);
+    c->t += h;
+}
+
+// Transition reduced density matrices of every atom between bra and ket
+// (same tree): T_a(s', s) = sum over the other atoms of conj(bra[s', ...])
+// ket[s, ...], out[9 a + s' + 3 s] (column-major 3 x 3).  Upward overlap
+// environments M_k (bra bond x ket bond) from the leaves, downward ones from
+// the root (a leaf's downward environment is its T_a); FP64.
+void transition_rdms(ttn_ctx* ket, ttn_ctx* bra, std::vector<zc>& out, std::vector<void*>& temp,
+                     std::vector<cplx*>& up, std::vector<cplx*>& dn) {
+    ForceFp64 f64;
+    ttn_ctx* c = ket;
+    const int nn = (int)c->nodes.size();
+    auto buf = [&](size_t n) {
+        void* p = nullptr;
+        if (test_take_alloc_fail() || cudaMalloc(&p, sizeof(cplx) * std::max<size_t>(n, 1)) != cudaSuccess)
+            throw TtnError(TTN_ERR_ALLOC, "transition environments");
+        temp.push_back(p);
+        return (cplx*)p;
+    };
+    if (up.empty()) {
+        up.assign(nn, nullptr);
+        dn.assign(nn, nullptr);
+        for (int k = 0; k < nn; ++k) {
+            const int D = c->nodes[k].d[2];
+            up[k] = buf((size_t)D * D);
+            dn[k] = buf((size_t)D * D);
+        }
+        dn.resize(nn + c->n_leaves);
+        for (int l = 0; l < c->n_leaves; ++l) dn[nn + l] = buf(9);
+    }
+    // W = M_{ch0} x_0 ket_k, M_{ch1} x_1 W (leaves: identity), with the
+    // legs in `skip` left open
+    auto dress = [&](int k, int skip, const cplx*& cur, int* d) {
+        const Node& nd = c->nodes[k];
+        cur = c->T[k];
+        for (int u = 0; u < 3; ++u) d[u] = nd.d[u];
+        cplx* bufs[2] = {c->tmp[0], c->tmp[1]};
+        int bi = 0;
+        for (int u = 0; u < 2; ++u) {
+            const int ch = nd.child[u];
+            if (ch < 0 || u == skip) continue;
+            leg_apply(c, up[ch], nd.d[u], cur, d, u, bufs[bi], 0.0);
+            cur = bufs[bi];
+            bi ^= 1;
+        }
+        return bi;
+    };
+    for (auto& lev : c->level_nodes)
+        for (int k : lev) {
+            const cplx* cur;
+            int d[3];
+            dress(k, -1, cur, d);
+            project(c, bra->T[k], bra->nodes[k].d, cur, d, 2, up[k], 1, 0, 0);
+        }
+    // downward: D_root = [[1]]; child u of k: contract bra_k with the other
+    // child's M and the parent's D applied to ket_k, leave leg u open
+    const cplx one = C(1.0);
+    CUDA_OK(cudaMemcpyAsync(dn[c->root], &one, sizeof(cplx), cudaMemcpyHostToDevice, c->stream));
+    for (int li = (int)c->level_nodes.size() - 1; li >= 0; --li)
+        for (int k : c->level_nodes[li]) {
+            const Node& nd = c->nodes[k];
+            for (int u = 0; u < 2; ++u) {
+                const int ch = nd.child[u];
+                const int other = 1 - u;
+                const cplx* cur = c->T[k];
+                int d[3] = {nd.d[0], nd.d[1], nd.d[2]};
+                cplx* bufs[2] = {c->tmp[0], c->tmp[1]};
+                int bi = 0;
+                if (nd.child[other] >= 0) {
+                    leg_apply(c, up[nd.child[other]], nd.d[other], cur, d, other, bufs[bi], 0.0);
+                    cur = bufs[bi];
+                    bi ^= 1;
+                }
+                if (k != c->root) {
+                    leg_apply(c, dn[k], nd.d[2], cur, d, 2, bufs[bi], 0.0);
+                    cur = bufs[bi];
+                    bi ^= 1;
+                }
+                cplx* dst = ch >= 0 ? dn[ch] : dn[nn + (-ch - 1)];
+                project(c, bra->T[k], bra->nodes[k].d, cur, d, u, dst, 1, 0, 0);
+            }
+        }
+    std::vector<cplx> h(9 * (size_t)c->n_leaves);
+    for (int l = 0; l < c->n_leaves; ++l)
+        CUDA_OK(cudaMemcpyAsync(h.data() + 9 * l, dn[nn + l], 9 * sizeof(cplx), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+    out.assign(9 * (size_t)c->N, zc(0.0));
+    for (int l = 0; l < c->n_leaves; ++l) {
+        const int a = c->leaf_atom[l];
+        if (a < 0) continue;
+        for (int e = 0; e < 9; ++e) out[9 * (size_t)a + e] = zc(h[9 * l + e].x, h[9 * l + e].y);
+    }
+}
+
+// A scratch context with c's lattice, bond dimension, Hamiltonian, schedule,
+// precision and stream.
+ttn_ctx* clone_config(ttn_ctx* c) {
+    ttn_ctx* s = nullptr;
+    ttn_status st = ttn_create(c->Lx, c->Ly, 3, c->chi, &s);
+    if (st != TTN_OK) throw TtnError(st, "gradient: scratch context");
+    auto chk = [&](ttn_status r, const char* what) {
+        if (r != TTN_OK) {
+            std::string m = std::string("gradient: ") + what + ": " + s->err;
+            ttn_destroy(s);
+            throw TtnError(r, m);
+        }
+    };
+    chk(ttn_set_stream(s, c->stream), "stream");
+    chk(ttn_set_precision(s, c->prec), "precision");
+    chk(ttn_set_hamiltonian(s, c->xy.data(), c->C6, c->r_cut), "hamiltonian");
+    chk(ttn_apply_pulse(s, c->schedule.data(), (int)c->schedule.size()), "pulse");
+    return s;
+}
+
+}  // namespace
+
+ttn_status ttn_fidelity_gradient(ttn_ctx* c, const ttn_ctx* target, double dt, int n_steps, int n_params,
+                                 const int* rows, const int* fields, int n_quad, int checkpoint_every, double* F,
+                                 double* grad) {
+    if (!c || !target || !F || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 1 || n_params < 0 ||
+        (n_params > 0 && (!rows || !fields || !grad)) || n_quad < 1 || n_quad > 8 || target->Lx != c->Lx ||
+        target->Ly != c->Ly || target->chi != c->chi || c->gamma != 0.0)
+        return TTN_ERR_ARG;
+    for (int p = 0; p < n_params; ++p)
+        if (rows[p] < 0 || rows[p] >= (int)c->schedule.size() || (fields[p] != 0 && fields[p] != 1))
+            return TTN_ERR_ARG;
+    ttn_ctx* tgt = const_cast<ttn_ctx*>(target);
+    return guard(c, [&] {
+        if (tgt->centre != tgt->root) throw TtnError(TTN_ERR_STATE, "target centre is not at its root");
+        if (tgt->stream != c->stream) CUDA_OK(cudaStreamSynchronize(tgt->stream));
+        std::vector<void*> temp;
+        std::vector<ttn_ctx*> scratch;
+        struct Free {
+            std::vector<void*>& t;
+            std::vector<ttn_ctx*>& s;
+            ~Free() {
+                for (void* p : t) cudaFree(p);
+                for (ttn_ctx* x : s) ttn_destroy(x);
+            }
+        } fr{temp, scratch};
+        const int N = n_steps;
+        const int L = checkpoint_every > 0 ? checkpoint_every : std::max(1, (int)std::ceil(std::sqrt((double)N)));
+        const double t0 = c->t;
+        // derivative operators dH/dtheta_p (3 x 3, column-major, |0>,|1>,|r>)
+        std::vector<std::array<zc, 9>> E(n_params);
+        for (int p = 0; p < n_params; ++p) {
+            E[p].fill(zc(0.0));
+            const ttn_pulse& row = c->schedule[rows[p]];
+            if (fields[p] == 0) {
+                const zc e = std::polar(1.0, row.phase_r);
+                E[p][2 + 3 * 1] = e;              // |r><1|
+                E[p][1 + 3 * 2] = std::conj(e);   // |1><r|
+            } else {
+                E[p][2 + 3 * 2] = zc(-1.0);       // -|r><r|
+            }
+        }
+        std::vector<double> gx, gw;
+        gauss_legendre(n_quad, gx, gw);
+        // forward pass with checkpoints every L steps
+        StateCopy start;
+        save_state(c, start, temp);
+        std::vector<StateCopy> cps((N + L - 1) / L);
+        for (int n = 0; n < N; ++n) {
+            if (n % L == 0) save_state(c, cps[n / L], temp);
+            step_at(c, t0 + (n + 0.5) * dt, dt);
+        }
+        const zc A = overlap(c, tgt);
+        std::vector<double> g(n_params, 0.0);
+        if (n_params > 0) {
+            ttn_ctx* chi = clone_config(c);
+            scratch.push_back(chi);
+            ttn_ctx* pw = clone_config(c);
+            scratch.push_back(pw);
+            ttn_ctx* cw = clone_config(c);
+            scratch.push_back(cw);
+            // chi_N = target
+            for (size_t k = 0; k < c->nodes.size(); ++k)
+                CUDA_OK(cudaMemcpyAsync(chi->T[k], tgt->T[k], sizeof(cplx) * c->nodes[k].s, cudaMemcpyDeviceToDevice,
+                                        c->stream));
+            chi->centre = chi->root;
+            chi->t = t0 + N * dt;
+            rebuild_up_envs(chi);
+            std::vector<StateCopy> seg(L);
+            StateCopy chis;
+            std::vector<zc> T;
+            std::vector<cplx*> up, dn;
+            for (int cp = (int)cps.size() - 1; cp >= 0; --cp) {
+                // states psi_{cp L} .. psi_{cp L + len - 1} of this segment
+                const int n0 = cp * L, len = std::min(L, N - n0);
+                load_state(c, cps[cp]);
+                for (int i = 0; i < len; ++i) {
+                    save_state(c, seg[i], temp);
+                    if (i + 1 < len) step_at(c, t0 + (n0 + i + 0.5) * dt, dt);
+                }
+                for (int i = len - 1; i >= 0; --i) {
+                    const int n = n0 + i;               // step n: psi_n -> psi_{n+1}
+                    const double tm = t0 + (n + 0.5) * dt;
+                    std::vector<int> act;
+                    for (int p = 0; p < n_params; ++p) {
+                        const ttn_pulse& row = c->schedule[rows[p]];
+                        if (row.t0 <= tm && tm < row.t1) act.push_back(p);
+                    }
+                    if (!act.empty()) {
+                        save_state(chi, chis, temp);
+                        std::vector<zc> acc(n_params, zc(0.0));
+                        for (int j = 0; j < n_quad; ++j) {
+                            const double sj = 0.5 * dt * (1.0 + gx[j]);
+                            load_state(pw, seg[i]);
+                            step_at(pw, tm, sj);                 // psi(s_j)
+                            load_state(cw, chis);
+                            step_at(cw, tm, -(dt - sj));         // chi(s_j)
+                            transition_rdms(pw, cw, T, temp, up, dn);
+                            for (int p : act) {
+                                const int a = c->schedule[rows[p]].atom;
+                                zc v(0.0);
+                                for (int e = 0; e < 9; ++e) v += E[p][e] * T[9 * (size_t)a + e];
+                                acc[p] += 0.5 * dt * gw[j] * v;
+                            }
+                        }
+                        for (int p : act) g[p] += 2.0 * (std::conj(A) * (zc(0.0, -1.0) * acc[p])).real();
+                    }
+                    step_at(chi, tm, -dt);                      // chi_n = U_{n+1}^H chi_{n+1}
+                }
+            }
+        }
+        // restore the context's state and time
+        load_state(c, start);
+        sync_check(c);
+        *F = std::norm(A);
+        for (int p = 0; p < n_params; ++p) grad[p] = g[p];
     });
 }
 

@@ -34,6 +34,8 @@ SIGNATURES = [
     ("ttn_set_decay", ctypes.c_int, [_P, ctypes.c_double]),
     ("ttn_compress", ctypes.c_int, [_P, _P, _D]),
     ("ttn_sample", ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
+    ("ttn_fidelity_gradient", ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _I, _I,
+                                              ctypes.c_int, ctypes.c_int, _D, _D]),
     ("ttn_set_product_state", ctypes.c_int, [_P, _D]),
     ("ttn_set_ghz_target", ctypes.c_int, [_P, _I, ctypes.c_double]),
     ("ttn_tdvp_step", ctypes.c_int, [_P, ctypes.c_double]),
@@ -293,6 +295,23 @@ class TTN:
                                         out.ctypes.data_as(_I)), "sample")
         return out
 
+    GRAD_FIELDS = {"omega_r": 0, "delta": 1}
+
+    def fidelity_gradient(self, target, dt, n_steps, params, n_quad=6, checkpoint_every=0):
+        """(F, dF/dtheta) of F = |<target|psi(t + n_steps dt)>|^2 from the
+        current state; params: (schedule row, "omega_r" | "delta") pairs.
+        The state and time are unchanged afterwards."""
+        n = len(params)
+        rows = np.ascontiguousarray([int(r) for r, _ in params], dtype=np.int32)
+        fields = np.ascontiguousarray([self.GRAD_FIELDS.get(f, f) for _, f in params], dtype=np.int32)
+        F = np.zeros(1)
+        g = np.zeros(max(1, n))
+        self._check(self.lib.ttn_fidelity_gradient(self.h, target.h, float(dt), int(n_steps), n,
+                                                   rows.ctypes.data_as(_I), fields.ctypes.data_as(_I),
+                                                   int(n_quad), int(checkpoint_every), _dptr(F), _dptr(g)),
+                    "fidelity_gradient")
+        return float(F[0]), g[:n].copy()
+
     def overlap(self, target):
         out = np.zeros(2)
         self._check(self.lib.ttn_overlap(self.h, target.h, _dptr(out)), "overlap")
@@ -385,14 +404,14 @@ class TTN:
         return {"krylov_runs": vals[0], "matvecs": vals[1], "max_krylov_err": float(max_err),
                 "launches": vals[3], "qr_calls": vals[4], "completed_columns": vals[5]}
 
-    PROFILE_KINDS = ("tc_gemm", "split_pack", "f64_gemm", "qr")
+    PROFILE_KINDS = ("tc_gemm", "split_pack", "f64_gemm", "qr", "krylov_vectors")
 
     def profile_begin(self):
         self._check(self.lib.ttn_profile_begin(self.h), "profile_begin")
 
     def profile_end(self):
-        out = np.zeros(16)
-        self._check(self.lib.ttn_profile_end(self.h, _dptr(out), 16), "profile_end")
+        out = np.zeros(4 * len(self.PROFILE_KINDS))
+        self._check(self.lib.ttn_profile_end(self.h, _dptr(out), out.size), "profile_end")
         return {k: {"launches": int(out[4 * i]), "ms": out[4 * i + 1], "flops": out[4 * i + 2],
                     "bytes": out[4 * i + 3]} for i, k in enumerate(self.PROFILE_KINDS)}
 
