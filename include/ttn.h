@@ -248,10 +248,12 @@ ttn_status ttn_get_stats(const ttn_ctx* ctx, int64_t* out6);
 /* Kernel-level timing with CUDA events recorded on the context's stream.
  * Between begin and end every contraction launch, every QR and every group of
  * Krylov vector kernels is bracketed by an event pair.  ttn_profile_end
- * synchronises and fills out[4 * min(5, n / 4)] with, for kind k = 0
+ * synchronises and fills out[4 * min(6, n / 4)] with, for kind k = 0
  * tensor-core GEMM (tcgen05), 1 split-operand packing, 2 FP64 GEMM, 3 QR,
  * 4 Krylov vector work (re-orthogonalisation, scalars, combination, one-block
- * runs of small nodes): out[4k + 0] event pairs, [4k + 1] summed device time
+ * runs of small nodes), 5 the other element-wise kernels of the sweep (block
+ * assembly, leg permutations, absorb norms): out[4k + 0] event
+ * pairs, [4k + 1] summed device time
  * in ms, [4k + 2] algorithmic flops (8 M N K per complex contraction;
  * 16 M D^2 per QR), [4k + 3] algorithmic bytes.  n must be >= 16 (kinds that
  * do not fit are left out). */

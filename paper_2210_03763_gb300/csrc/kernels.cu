@@ -20,6 +20,28 @@ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
 __device__ __forceinline__ cplx cdotc(cplx a, cplx b) {
     return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
+// The vector kernels below are bound by GB300's FP64 pipe (about 1/64 of its
+// FP32 rate), not by HBM, so the complex multiply-accumulates are written as
+// four fused multiply-adds (s += conj(a) b, x -= a h) instead of two
+// multiplies, two fused operations and two adds.
+__device__ __forceinline__ void acc_cdotc(cplx& s, cplx a, cplx b) {
+    s.x = fma(a.x, b.x, s.x);
+    s.x = fma(a.y, b.y, s.x);
+    s.y = fma(a.x, b.y, s.y);
+    s.y = fma(-a.y, b.x, s.y);
+}
+__device__ __forceinline__ void sub_cmul(cplx& x, cplx a, cplx h) {
+    x.x = fma(-a.x, h.x, x.x);
+    x.x = fma(a.y, h.y, x.x);
+    x.y = fma(-a.x, h.y, x.y);
+    x.y = fma(-a.y, h.x, x.y);
+}
+__device__ __forceinline__ void acc_cmul(cplx& x, cplx a, cplx h) {
+    x.x = fma(a.x, h.x, x.x);
+    x.x = fma(-a.y, h.y, x.x);
+    x.y = fma(a.x, h.y, x.y);
+    x.y = fma(a.y, h.x, x.y);
+}
 
 __device__ __forceinline__ void chunk_of(long long n, int G, long long& lo, long long& hi) {
     long long c = (n + G - 1) / G;
@@ -94,7 +116,7 @@ __global__ void dots_kernel(cplx* V, long long ld, int nv, const cplx* w, long l
         cplx s = make_double2(0.0, 0.0);
         if (i != skip_col) {
             const cplx* vi = V + (long long)i * ld;
-            for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s = cadd(s, cdotc(vi[e], w[e]));
+            for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) acc_cdotc(s, vi[e], w[e]);
         }
         s = block_sum_c(s, sh);
         if (threadIdx.x == 0) partial[(long long)i * G + blockIdx.x] = s;
@@ -125,9 +147,7 @@ __global__ void orth_update_kernel(const cplx* V, long long ld, int nv, const cp
         cplx x = w[e];
         for (int i = 0; i < nv; ++i) {
             if (i == skip_col) continue;
-            cplx p = cmul(V[(long long)i * ld + e], sh_h[i]);
-            x.x -= p.x;
-            x.y -= p.y;
+            sub_cmul(x, V[(long long)i * ld + e], sh_h[i]);
         }
         w[e] = x;
     }
@@ -137,7 +157,7 @@ __global__ void orth_update_kernel(const cplx* V, long long ld, int nv, const cp
             cplx s = make_double2(0.0, 0.0);
             if (i != skip_col) {
                 const cplx* vi = V + (long long)i * ld;
-                for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s = cadd(s, cdotc(vi[e], w[e]));
+                for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) acc_cdotc(s, vi[e], w[e]);
             }
             s = block_sum_c(s, shc);
             if (threadIdx.x == 0) partial_dots[(long long)i * G + blockIdx.x] = s;
@@ -199,7 +219,7 @@ __global__ void combine_kernel(const cplx* V, long long ld, int nv, const Krylov
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         cplx s = make_double2(0.0, 0.0);
-        for (int i = 0; i < nv; ++i) s = cadd(s, cmul(V[(long long)i * ld + e], c[i]));
+        for (int i = 0; i < nv; ++i) acc_cmul(s, V[(long long)i * ld + e], c[i]);
         y[e] = s;
     }
 }

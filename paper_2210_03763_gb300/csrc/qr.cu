@@ -605,9 +605,11 @@ __device__ void la_dots(int P, PairF pair, cplx* out, const cplx* A, long long M
 }
 
 __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D, cplx* R, int* flags, cplx* part,
-                                                     cplx* red_out, unsigned* bar, int* err, int nc_max, double tol) {
+                                                     cplx* red_out, unsigned* bar, int* err, int nc_max, double tol,
+                                                     int la_max) {
     // dynamic shared memory: nc_max cached columns of QCS rows, then the
-    // look-ahead window (this block's rows of v1_j)
+    // look-ahead window of at most la_max (<= LA_WMAX) columns (this block's
+    // rows of v1_j)
     extern __shared__ cplx dyn[];
     cplx* qc = dyn;
     cplx(*vw)[QB] = reinterpret_cast<cplx(*)[QB]>(dyn + (long long)nc_max * QCS);
@@ -634,7 +636,7 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
     if (t == 0) sm.nnz = 0;
     __syncthreads();
     int seq = 0;        // reductions so far: partial rows alternate between two buffers
-    int la_w = 4;       // look-ahead window width
+    int la_w = min(4, la_max);   // look-ahead window width
     for (int k = 0; k < D; ++k) {
         const int n = sm.nnz, E = 2 * n + 2;
         const int nc = min(n, nc_max);
@@ -706,7 +708,7 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
             const int nq = sm.nnz, ncq = min(nq, nc_max);
             const int cap = (PSTRIDE - nq - 1) / (nq + 2);   // widest window whose sums fit a partial row
             if (k0 == k + 1 && cap < 2) break;    // kept set too wide: stay column by column (state in place)
-            const int W = min(min(min(la_w, LA_WMAX), D - k0), cap);   // >= 1
+            const int W = min(min(min(la_w, la_max), D - k0), cap);   // >= 1
             const bool after = k0 + W < D;
             const int ka = k0 + W;                // the column after the window
             // L1: g_j = Q^H a_j, kept in la_g; v1_j = a_j - Q g_j into vw
@@ -793,10 +795,10 @@ __global__ void __launch_bounds__(QB) qr_coop_kernel(cplx* A, long long M, int D
             __syncthreads();
             if (js < 0) {   // the whole window was dependent
                 k0 += W;
-                la_w = min(2 * la_w, LA_WMAX);
+                la_w = min(2 * la_w, la_max);
                 continue;
             }
-            la_w = max(4, la_w / 2);
+            la_w = max(min(4, la_max), la_w / 2);
             const int kn = k0 + js + 1;           // next column, back in the one-column loop
             if (kn >= D) {
                 k0 = D;
@@ -1171,8 +1173,13 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
     // one cooperative launch for the column loop when all G blocks fit on
     // the GPU at once (with as many cached columns per block as allows);
     // otherwise three launches per column
-    static int coop_limit[3] = {-1, -1, -1};   // max co-resident blocks at QC_MAX, 8, 0 cached columns
-    static const int nc_opts[3] = {QC_MAX, 8, 0};
+    // launch options: cached columns and look-ahead window; the smaller
+    // shared-memory footprints let more row blocks be co-resident (with no
+    // cached columns and a window of 4, 65536-row matrices of bond dimension
+    // 256 fit in one cooperative launch)
+    static int coop_limit[4] = {-1, -1, -1, -1};   // max co-resident blocks per option
+    static const int nc_opts[4] = {QC_MAX, 8, 0, 0};
+    static const int la_opts[4] = {LA_WMAX, LA_WMAX, LA_WMAX, 4};
     if (coop_limit[0] < 0) {
         int dev = 0, nsm = 0, coop = 0;
         cudaGetDevice(&dev);
@@ -1180,22 +1187,22 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(cplx) * (QC_MAX * QCS + LA_WMAX * QB)));
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 4; ++i) {
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, QB,
-                                                          sizeof(cplx) * (nc_opts[i] * QCS + LA_WMAX * QB));
+                                                          sizeof(cplx) * (nc_opts[i] * QCS + la_opts[i] * QB));
             coop_limit[i] = coop ? nsm * per_sm : 0;
         }
     }
     bool coop_done = false;
-    for (int i = 0; i < 3 && !coop_done && D <= MAXD; ++i) {
+    for (int i = 0; i < 4 && !coop_done && D <= MAXD; ++i) {
         if (G > coop_limit[i]) continue;
-        int nc = nc_opts[i];
-        size_t smem = sizeof(cplx) * (nc * QCS + LA_WMAX * QB);
+        int nc = nc_opts[i], la = la_opts[i];
+        size_t smem = sizeof(cplx) * (nc * QCS + la * QB);
         // the barrier leaves its arrival count at zero after every completed
         // wait, so it needs a reset only after an error
         void* args[] = {(void*)&A, (void*)&MM, (void*)&D, (void*)&R, (void*)&ws.flags, (void*)&ws.part,
-                        (void*)&ws.h, (void*)&ws.bar, (void*)&ws.err, (void*)&nc, (void*)&tol};
+                        (void*)&ws.h, (void*)&ws.bar, (void*)&ws.err, (void*)&nc, (void*)&tol, (void*)&la};
         coop_done = cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(G), dim3(QB), args, smem, s) ==
                     cudaSuccess;
         if (!coop_done) cudaGetLastError();   // clear and use the multi-launch path

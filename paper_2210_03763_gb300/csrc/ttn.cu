@@ -248,8 +248,9 @@ void grow_split_ws(ttn_ctx* c, size_t bytes) {
 
 // Profile kinds: 0 tensor-core GEMM, 1 split packing, 2 FP64 GEMM, 3 QR,
 // 4 Krylov vector work (re-orthogonalisation, scalars, combination, and the
-// one-block Krylov runs of small nodes).
-enum { PK_TC = 0, PK_PACK = 1, PK_F64 = 2, PK_QR = 3, PK_KRY = 4, PK_N = 5 };
+// one-block Krylov runs of small nodes), 5 the remaining element-wise
+// kernels of the sweep (block assembly, leg permutations, absorb norms).
+enum { PK_TC = 0, PK_PACK = 1, PK_F64 = 2, PK_QR = 3, PK_KRY = 4, PK_MISC = 5, PK_N = 6 };
 
 cudaEvent_t next_event(ttn_ctx* c) {
     if (c->ev_next == c->ev_pool.size()) {
@@ -896,6 +897,7 @@ void split_heff_apply(ttn_ctx* c, const SplitHeff& S, const cplx* x, cplx* y) {
 }
 
 void assemble(ttn_ctx* c, const Env& e, cplx* out) {
+    ProfScope ps(c, PK_MISC, 0.0, 0.0);
     c->stats[3] += k_assemble_block(out, e.has_H ? e.H : nullptr, e.D, e.nops, (int)e.sites.size(),
                                     e.d_sites, e.dops, (int)e.driven.size(), e.d_driven, c->d_coef, c->gamma,
                                     c->stream);
@@ -1223,6 +1225,7 @@ void qr_leg(ttn_ctx* c, int k, int o) {
     cplx* A = c->T[k];
     static const int PERM[3][3] = {{1, 2, 0}, {0, 2, 1}, {0, 1, 2}};
     if (o != 2) {
+        ProfScope ps(c, PK_MISC, 0.0, 32.0 * nd.s);
         c->stats[3] += k_permute3(c->T[k], c->tmp[0], nd.d[0], nd.d[1], nd.d[2], PERM[o][0], PERM[o][1],
                                   PERM[o][2], 0, c->stream);
         A = c->tmp[0];
@@ -1242,6 +1245,7 @@ void qr_leg(ttn_ctx* c, int k, int o) {
     c->stats[4] += 1;
     c->stats[5] += ndep;
     if (o != 2)
+        ProfScope ps(c, PK_MISC, 0.0, 32.0 * nd.s);
         c->stats[3] += k_permute3(c->tmp[0], c->T[k], nd.d[0], nd.d[1], nd.d[2], PERM[o][0], PERM[o][1],
                                   PERM[o][2], 1, c->stream);
 }
@@ -1261,6 +1265,7 @@ void absorb(ttn_ctx* c, int k, int leg, bool gauge_only = false) {
     if (c->prec == TTN_SPLIT_TF32X3 && !g_force_fp64 && !gauge_only) {
         c->stats[3] += k_norm2_partial(c->Rbuf, D * D, c->apr, c->stream);
         leg_apply(c, c->Rbuf, nd.d[leg], c->T[k], nd.d, leg, c->tmp[1], 0.0);
+        ProfScope ps(c, PK_MISC, 0.0, 48.0 * nd.s);
         c->stats[3] += k_norm2_partial(c->tmp[1], nd.s, c->apx, c->stream);
         c->stats[3] += k_rescale_to_norm(c->tmp[1], nd.s, c->apx, red_blocks_for(nd.s), c->apr,
                                          red_blocks_for(D * D), c->stream);

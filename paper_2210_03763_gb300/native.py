@@ -404,7 +404,7 @@ class TTN:
         return {"krylov_runs": vals[0], "matvecs": vals[1], "max_krylov_err": float(max_err),
                 "launches": vals[3], "qr_calls": vals[4], "completed_columns": vals[5]}
 
-    PROFILE_KINDS = ("tc_gemm", "split_pack", "f64_gemm", "qr", "krylov_vectors")
+    PROFILE_KINDS = ("tc_gemm", "split_pack", "f64_gemm", "qr", "krylov_vectors", "elementwise")
 
     def profile_begin(self):
         self._check(self.lib.ttn_profile_begin(self.h), "profile_begin")

@@ -6,8 +6,9 @@ Shapes span several 128-row blocks with a ragged tail, full rank, low rank
 with the structured completion (kept rank <= 64) and with the sequential one
 (kept rank > 64), the zero matrix, a caller-given candidate order, the
 degenerate 1 x 1 case, the largest node matricisation of an 8x8 chi=128 TTN
-(16384 x 128) and a tall matrix with more row blocks than fit on the GPU at
-once (the multi-launch column loop).  Both sides work in FP64 and take every
+(16384 x 128), the widest one at chi = 256 (65536 x 256, one cooperative
+launch with the smallest shared-memory option) and a tall matrix with more
+row blocks than fit on the GPU at once (the multi-launch column loop).  Both sides work in FP64 and take every
 dependence and candidate decision from values far from their thresholds, so
 Q and R agree to rounding: 1e-11 of max|A| for R, 1e-10 absolute for Q.
 """
@@ -119,6 +120,18 @@ def test_largest_node_matricisation(native):
     A = _cmat(rng, 16384, 3) @ _cmat(rng, 3, 128)
     nd, ms = _check(native, A, expect_dep=125)
     print("16384 x 128 rank 3: %.3f ms" % ms)
+
+
+def test_widest_node_matricisation_one_launch(native):
+    # 65536 x 256: the level-3/4 node of an 8x8, chi = 256 TTN.  512 row
+    # blocks fit in one cooperative launch only with the smallest
+    # shared-memory option (no cached columns, look-ahead window of 4).
+    rng = np.random.default_rng(8)
+    A = _cmat(rng, 65536, 2) @ _cmat(rng, 2, 256)
+    nd, ms = _check(native, A, expect_dep=254)
+    print("65536 x 256 rank 2: %.3f ms" % ms)
+    nd, ms = _check(native, _cmat(rng, 65536, 256), expect_dep=0)
+    print("65536 x 256 full rank: %.3f ms" % ms)
 
 
 def test_more_row_blocks_than_resident(native):
