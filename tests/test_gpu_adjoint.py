@@ -159,7 +159,7 @@ def test_autograd_function_returns_the_abi_gradient(native):
     g.apply_pulse(sched)
     g.set_product_state(plus)
     F0, g0 = g.fidelity_gradient(t, dt, n_steps, params, n_quad=8)
-    assert abs(float(F) - F0) < 1e-14
+    assert abs(float(F.detach()) - F0) < 1e-14
     assert np.allclose(theta.grad.numpy(), g0, rtol=0, atol=1e-14)
     g.close()
     t.close()
