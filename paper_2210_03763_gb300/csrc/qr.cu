@@ -1128,6 +1128,103 @@ __global__ void __launch_bounds__(SC_THREADS) sc_select_kernel(const cplx* A, lo
     }
 }
 
+// The same selection by one warp, for kept ranks r <= 32 (lane j holds
+// w_j and y_j): no block-wide barriers in the candidate loop, whose latency
+// dominated the block version (one candidate evaluation per dependent column
+// is typical).  Every sum runs in the block version's order, so both take
+// identical decisions and produce identical Y, nu.
+__global__ void __launch_bounds__(32) sc_select_warp_kernel(const cplx* A, long long M, const int* kept, int r,
+                                                            int m, const int* cand, int ncand, int* acc_rows,
+                                                            cplx* Y, double* nu, int* row_rank, int* cand_used) {
+    extern __shared__ cplx sm[];
+    cplx* Mi = sm;          // r x r
+    cplx* ys = Mi + r * r;  // r
+    const int lane = threadIdx.x;
+    for (int i = lane; i < r * r; i += 32) Mi[i] = make_double2((i / r == i % r) ? 1.0 : 0.0, 0.0);
+    __syncwarp();
+    const long long kl = lane < r ? (long long)kept[lane] : 0;
+    // residual 1 - w M w^H of candidate row c; y (this lane's entry) = M conj(w)
+    auto residual = [&](int c, cplx& yl) -> double {
+        const cplx wl = lane < r ? A[c + kl * M] : make_double2(0.0, 0.0);
+        cplx s = make_double2(0.0, 0.0);
+        for (int j = 0; j < r; ++j) {
+            cplx wj;
+            wj.x = __shfl_sync(0xffffffffu, wl.x, j);
+            wj.y = __shfl_sync(0xffffffffu, wl.y, j);
+            if (lane < r) {
+                const cplx mm = Mi[lane * r + j];
+                s.x += mm.x * wj.x + mm.y * wj.y;
+                s.y += mm.y * wj.x - mm.x * wj.y;
+            }
+        }
+        yl = s;
+        double acc = lane < r ? wl.x * s.x - wl.y * s.y : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        return 1.0 - __shfl_sync(0xffffffffu, acc, 0);
+    };
+    int p = 0;
+    for (int t = 0; t < m; ++t) {
+        int chosen = -1;
+        double res = 0.0;
+        cplx yl = make_double2(0.0, 0.0);
+        for (; p < ncand; ++p) {
+            if (cand_used[p]) continue;
+            res = residual(cand[p], yl);
+            if (res >= MIN_RES2) {
+                chosen = p;
+                break;
+            }
+        }
+        if (chosen < 0) {
+            // no candidate reaches 1/4: the largest residual, earliest on ties
+            double best = -1.0;
+            int bi = -1;
+            for (int q = 0; q < ncand; ++q) {
+                if (cand_used[q]) continue;
+                cplx yq;
+                const double rq = residual(cand[q], yq);
+                if (rq > best) {
+                    best = rq;
+                    bi = q;
+                }
+            }
+            // non-finite residuals: the first unused candidate (indices stay in bounds)
+            chosen = bi;
+            if (chosen < 0)
+                for (int q = 0; q < ncand; ++q)
+                    if (!cand_used[q]) {
+                        chosen = q;
+                        break;
+                    }
+            if (chosen < 0) chosen = 0;
+            res = residual(cand[chosen], yl);
+            p = ncand;
+        } else {
+            ++p;
+        }
+        const int c = cand[chosen];
+        if (lane == 0) {
+            acc_rows[t] = c;
+            nu[t] = sqrt(res);
+            row_rank[c] = t;
+            cand_used[chosen] = 1;
+        }
+        if (lane < r) {
+            Y[(long long)t * r + lane] = yl;
+            ys[lane] = yl;
+        }
+        __syncwarp();
+        const double inv = 1.0 / res;
+        for (int idx = lane; idx < r * r; idx += 32) {
+            const int i = idx / r, j = idx % r;   // M += y y^H / res
+            const cplx yi = ys[i], yj = ys[j];
+            Mi[idx].x += inv * (yi.x * yj.x + yi.y * yj.y);
+            Mi[idx].y += inv * (yi.y * yj.x - yi.x * yj.y);
+        }
+        __syncwarp();
+    }
+}
+
 // U[:, t] = (e_{a_t} - (Q_r y_t, rows accepted before t zeroed)) / nu_t
 __global__ void __launch_bounds__(QB) sc_materialize_kernel(cplx* A, long long M, const int* kept, int r,
                                                             const int* dep, int m, const cplx* Y, const double* nu,
@@ -1252,16 +1349,21 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
         cudaMemcpyAsync(ws.dep, hd, sizeof(int) * nd, cudaMemcpyHostToDevice, s);
         int gi = (int)std::min<long long>((std::max<long long>(MM, ncand) + 255) / 256, 1024);
         sc_init_kernel<<<gi, 256, 0, s>>>(ws.row_rank, MM, ws.cand_used, ncand);
-        size_t sel_smem = sizeof(cplx) * ((size_t)r * r + 2 * (size_t)r + 2);
-        sc_select_kernel<<<1, SC_THREADS, sel_smem, s>>>(A, MM, ws.kept, r, nd, cand, ncand, ws.acc_rows, ws.Y,
-                                                         ws.nu, ws.row_rank, ws.cand_used);
-        size_t mat_smem = sizeof(cplx) * (size_t)r * nd + 16;
-        static bool attr = false;
+        static bool attr = false;   // shared memory above 48 KB (kept rank up to 64)
         if (!attr) {
             cudaFuncSetAttribute(sc_materialize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 64);
             cudaFuncSetAttribute(sc_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
             attr = true;
         }
+        if (r <= 32) {
+            sc_select_warp_kernel<<<1, 32, sizeof(cplx) * ((size_t)r * r + (size_t)r + 1), s>>>(
+                A, MM, ws.kept, r, nd, cand, ncand, ws.acc_rows, ws.Y, ws.nu, ws.row_rank, ws.cand_used);
+        } else {
+            size_t sel_smem = sizeof(cplx) * ((size_t)r * r + 2 * (size_t)r + 2);
+            sc_select_kernel<<<1, SC_THREADS, sel_smem, s>>>(A, MM, ws.kept, r, nd, cand, ncand, ws.acc_rows, ws.Y,
+                                                             ws.nu, ws.row_rank, ws.cand_used);
+        }
+        size_t mat_smem = sizeof(cplx) * (size_t)r * nd + 16;
         sc_materialize_kernel<<<G, QB, mat_smem, s>>>(A, MM, ws.kept, r, ws.dep, nd, ws.Y, ws.nu, ws.acc_rows,
                                                       ws.row_rank);
         launches += 3;

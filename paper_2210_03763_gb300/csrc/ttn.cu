@@ -1244,10 +1244,11 @@ void qr_leg(ttn_ctx* c, int k, int o) {
     }
     c->stats[4] += 1;
     c->stats[5] += ndep;
-    if (o != 2)
+    if (o != 2) {
         ProfScope ps(c, PK_MISC, 0.0, 32.0 * nd.s);
         c->stats[3] += k_permute3(c->tmp[0], c->T[k], nd.d[0], nd.d[1], nd.d[2], PERM[o][0], PERM[o][1],
                                   PERM[o][2], 1, c->stream);
+    }
 }
 
 // node k <- Rbuf x_leg node k   (absorb the link matrix).
