@@ -5,7 +5,7 @@ vector (Oracle-X).  Test infrastructure only (see the package docstring).
 This is the reference for gradients of the discrete time-stepping map
 (differentiate the discretised evolution, not the continuous one): with
 steps U_n = exp(-i H(t_n + dt/2) dt) (the time discretisation of the TDVP
-step, reading A8) and
+step: H frozen at the step midpoint) and
 
     F(theta) = |<target| U_N ... U_1 |psi_0>|^2,
 

@@ -3,7 +3,7 @@
 State psi in C^(3^N) with basis index sum_i s_i 3^i (s_i in {0:|0>, 1:|1>, 2:|r>}),
 so atom 0 is the fastest index.  Time stepping is piecewise constant: step k
 uses H(t_k + dt/2) and psi <- exp(-i H dt) psi, the same time discretisation
-the TDVP step uses (reading A8).  The exponential is NOT a Krylov method:
+the TDVP step uses (H frozen at the step midpoint).  The exponential is NOT a Krylov method:
 
 * N <= 6: dense Hermitian eigendecomposition (numpy.linalg.eigh),
 * N <= 9: scipy.sparse.linalg.expm_multiply (Al-Mohy & Higham truncated Taylor).

@@ -2,9 +2,10 @@
 
 * ``qr_complete``  -- QR that moves the orthogonality centre (gauge move of
   Sec. "Tensor network simulations"), with the deterministic completion of
-  rank-deficient bases (reading A10).
+  rank-deficient bases (columns with residual <= 1e-10 |A|_F
+  replaced by unit vectors in a fixed candidate order).
 * ``krylov_expm``  -- Lanczos approximation of exp(z H) v (the local
-  propagator TDVP needs; Krylov parameters: reading A11).
+  propagator TDVP needs; Krylov parameters: m_max = 30, tolerance 1e-13).
 """
 import numpy as np
 

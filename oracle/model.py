@@ -12,10 +12,10 @@ Qutrit basis per atom: index 0 = |0>, 1 = |1>, 2 = |r>.
 * W_i = Omega^R_i exp(i phi_i) drives the single-photon 1<->r transition.
 * The detuning term -Delta n is not printed in Eq. 1; the CZ pulse of
   Sec. "Compiler for global GHZ states" uses a detuning on |r>, so it is added
-  here as -Delta n (reading A3).
+  here as -Delta n (the paper's pulse needs it; Eq. 1 omits it).
 * Eq. 1 sums over all ordered pairs; we read it as unordered pairs i<j without
-  self-interaction (reading A1).  Eq. 2 prints V = -C6/d^6; the caller passes
-  the signed coefficient, V_ij = C6/d^6 (reading A2).
+  self-interaction (Eq. 1's double sum read as unordered pairs).  Eq. 2 prints V = -C6/d^6; the caller passes
+  the signed coefficient, V_ij = C6/d^6.
 """
 import numpy as np
 
@@ -76,5 +76,5 @@ def coefficients(schedule, n_atoms, t):
 
 
 def local_term(ox, oz, w, delta):
-    """Single-atom part of Eq. 1 (plus -Delta n, reading A3) as a 3x3 matrix."""
+    """Single-atom part of Eq. 1 (plus the detuning term -Delta n) as a 3x3 matrix."""
     return ox * SX + oz * SZ + w * RP + np.conj(w) * RP.conj().T - delta * NR

@@ -7,12 +7,12 @@ simulations"; padding rule from Sec. "Parallel quantum algorithms").
   carry no Hamiltonian term and are never driven.
 * Level-0 nodes pair leaves (2i, 2i+1); level-l nodes pair level-(l-1) nodes;
   the single top node is the root, whose parent leg is a dummy leg of dim 1
-  (reading A14).
+  (the paper does not fix the tree shape: a balanced binary tree is used).
 * Bond dimension of the parent leg of a node whose subtree holds the atom set S:
   D = min(chi, 3^|S|, 3^|complement of S|) (only real atoms count).
 
 Hilbert curve: the iterative index->(x, y) map, starting at the (0, 0) corner
-(reading A13).  Written here from the curve's recursive definition; the CUDA
+(the paper does not fix the orientation).  Written here from the curve's recursive definition; the CUDA
 library has its own copy and a test checks that the two agree.
 """
 import numpy as np

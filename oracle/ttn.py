@@ -187,7 +187,7 @@ class OracleTTN:
     def _build_from_branches(self, leaf_branches, root_coef):
         """Node tensors from per-leaf branch vectors (3 x nb) combined with
         ``root_coef`` at the root; each node is the QR-completed isometry of its
-        branch columns (the deterministic completion of reading A10)."""
+        branch columns (the deterministic completion of rank-deficient bases)."""
         tr = self.tree
         B = {}
         for lev in tr.level_nodes:

@@ -18,7 +18,7 @@ instead of Lanczos) against the CPU oracle:
   because Arnoldi, unlike Lanczos, does not symmetrise the projected
   generator, so the anti-Hermitian part of the split contraction error moves
   the norm.  A product-state start is not used: its rank-deficient bonds are
-  completed from residuals near the dependence threshold (reading A10), so
+  completed from residuals near the dependence threshold of the completion rule, so
   two precisions can complete differently and then follow different, equally
   valid projected dynamics (measured 2e-6 infidelity without decay as well).
 """

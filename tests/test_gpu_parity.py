@@ -332,7 +332,7 @@ def test_heff_full_size_8x8_chi128_vs_oracle(native, full_size_heff_ref, prec, t
 # 20 steps of dt = 0.05 straddling the end of the control atoms' pi pulse and
 # the start of the target's 2 pi pulse.  Start: a seeded random TTN with every
 # bond at full rank, so that no QR of the sweep completes a rank-deficient
-# basis (near the 1e-10 dependence threshold those decisions, reading A10,
+# basis (near the 1e-10 dependence threshold those completion decisions
 # make product-state trajectories rounding-sensitive).  The oracle's final
 # tensors are loaded into a second context: |1 - |<oracle|gpu>|^2 / norms|
 # <= 1e-10, norms to 1e-12, populations and energy to 1e-10.

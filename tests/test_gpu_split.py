@@ -203,14 +203,15 @@ def test_split_tracks_fp64_from_a_product_state(native):
     # first step TDVP grows new bond directions from them; the split run's
     # node tensors carry ~5e-7 relative noise in the still-empty directions,
     # the QR keeps those columns (their residual is above the 1e-10
-    # dependence threshold of reading A10) where the FP64 run completes them
+    # dependence threshold of the completion rule) where the FP64 run completes them
     # by the deterministic rule, so the two runs project on different
     # tangent spaces from then on.  Measured: 1.9e-6 infidelity after one
     # step of 0.02, not growing over the next four (1.9e-6 after 5).  (A
     # split-only threshold of 1e-5 made it 2e-5: it also replaced real
     # directions still below 1e-5 by completion vectors.)  From |+>^N, whose
     # bonds grow symmetrically, the two precisions agree to 4e-12 over a
-    # whole CZ layer, and from full-rank starts to 1e-10.
+    # whole CZ layer (the 4x4, chi = 64 window of runs.py), and from full-rank
+    # starts to 1e-10.
     Lx = Ly = 4
     xy = W.square_lattice(Lx, Ly)
     sched, _ = W.cz_layer_workload(Lx, Ly, 2.0 ** 1.5)
