@@ -7,6 +7,7 @@
 #include "common.cuh"
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace {
 
@@ -847,11 +848,21 @@ int k_dense_heff(cplx* H, const int* d, const cplx* hb0, const cplx* hb1, const 
 int k_small_krylov(const cplx* H, int n, cplx* x, double zr, double zi, double tol, int mmax, int arnoldi,
                    KrylovScalars* ks, cudaStream_t s) {
     const size_t smem = sizeof(cplx) * ((size_t)n * n + (size_t)(mmax + 2) * n);
-    static bool attr = false;   // same limit on every device (shared memory per block)
-    if (!attr) {
-        cudaFuncSetAttribute(small_krylov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(cplx) * ((size_t)SMALL_S * SMALL_S + (size_t)(KRYLOV_MMAX + 2) * SMALL_S)));
-        attr = true;
+    // the shared-memory limit is a per-device attribute of the kernel: set it
+    // once on every device the process uses
+    static std::mutex mu;
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!attr[dev]) {
+            cudaFuncSetAttribute(small_krylov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(cplx) *
+                                       ((size_t)SMALL_S * SMALL_S + (size_t)(KRYLOV_MMAX + 2) * SMALL_S)));
+            attr[dev] = true;
+        }
     }
     small_krylov_kernel<<<1, SMALL_KRYLOV_THREADS, smem, s>>>(H, n, x, zr, zi, tol, mmax, arnoldi, ks);
     return 1;

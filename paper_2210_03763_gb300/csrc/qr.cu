@@ -34,6 +34,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace {
 
@@ -1274,12 +1275,21 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
     // shared-memory footprints let more row blocks be co-resident (with no
     // cached columns and a window of 4, 65536-row matrices of bond dimension
     // 256 fit in one cooperative launch)
-    static int coop_limit[4] = {-1, -1, -1, -1};   // max co-resident blocks per option
+    // (co-resident block counts and kernel attributes are per device: kept
+    // for every device the process uses)
+    static std::mutex dev_mu;
+    static int coop_limits[64][4];
+    static bool dev_ready[64] = {};
     static const int nc_opts[4] = {QC_MAX, 8, 0, 0};
     static const int la_opts[4] = {LA_WMAX, LA_WMAX, LA_WMAX, 4};
-    if (coop_limit[0] < 0) {
-        int dev = 0, nsm = 0, coop = 0;
-        cudaGetDevice(&dev);
+    int cur_dev = 0;
+    cudaGetDevice(&cur_dev);
+    if (cur_dev < 0 || cur_dev >= 64) cur_dev = 0;
+    std::unique_lock<std::mutex> dev_lock(dev_mu);
+    int* coop_limit = coop_limits[cur_dev];
+    if (!dev_ready[cur_dev]) {
+        dev_ready[cur_dev] = true;
+        int dev = cur_dev, nsm = 0, coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1291,6 +1301,7 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
             coop_limit[i] = coop ? nsm * per_sm : 0;
         }
     }
+    dev_lock.unlock();   // the limits of a device never change once set
     bool coop_done = false;
     for (int i = 0; i < 4 && !coop_done && D <= MAXD; ++i) {
         if (G > coop_limit[i]) continue;
@@ -1349,11 +1360,15 @@ int qr_cgs2(cplx* A, int M, int D, cplx* R, const int* cand, int ncand, QrScratc
         cudaMemcpyAsync(ws.dep, hd, sizeof(int) * nd, cudaMemcpyHostToDevice, s);
         int gi = (int)std::min<long long>((std::max<long long>(MM, ncand) + 255) / 256, 1024);
         sc_init_kernel<<<gi, 256, 0, s>>>(ws.row_rank, MM, ws.cand_used, ncand);
-        static bool attr = false;   // shared memory above 48 KB (kept rank up to 64)
-        if (!attr) {
-            cudaFuncSetAttribute(sc_materialize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 64);
-            cudaFuncSetAttribute(sc_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-            attr = true;
+        static bool attr[64] = {};   // shared memory above 48 KB (kept rank up to 64), per device
+        {
+            std::lock_guard<std::mutex> lock(dev_mu);
+            if (!attr[cur_dev]) {
+                cudaFuncSetAttribute(sc_materialize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     96 * 1024 + 64);
+                cudaFuncSetAttribute(sc_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+                attr[cur_dev] = true;
+            }
         }
         if (r <= 32) {
             sc_select_warp_kernel<<<1, 32, sizeof(cplx) * ((size_t)r * r + (size_t)r + 1), s>>>(
