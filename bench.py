@@ -428,10 +428,8 @@ def main():
     if args.full_rank_steps > 0 and rank == 0:
         # the same workload from a random full-rank isometric TTN: every QR is
         # full rank (the |+>^64 start keeps most bonds rank-deficient early on)
-        from oracle.tree import Tree   # tree shapes only (integer bookkeeping)
-        tr = Tree(LX, LY, CHI)
-        Ts = W.random_ttn_tensors([tr.shape(k) for k in range(tr.n_nodes)], 77)
         h = make_ctx(native, native.SPLIT_TF32X3, stream)
+        Ts = W.random_ttn_tensors([h.node_info(k)[0] for k in range(h.num_nodes())], 77)
         for k, X in enumerate(Ts):
             h.set_node(k, X)
         h.refresh_envs()
