@@ -161,7 +161,9 @@ ttn_status ttn_load(ttn_ctx* ctx, const char* path);
  * its own; its time is set to src's.  discarded (may be NULL) receives 2
  * doubles: the sum over bonds and the largest of the discarded weights
  * (dropped eigenvalues / trace of the bond density matrix).  The infidelity
- * of the truncation is at most (sum_bonds sqrt(weight))^2. */
+ * of the truncation is at most (sum_bonds sqrt(weight))^2.  src keeps its
+ * state (its centre moves to the root); after an error dst's state is
+ * undefined. */
 ttn_status ttn_compress(ttn_ctx* src, ttn_ctx* dst, double* discarded);
 
 /* Projective measurement of every atom in the {|0>, |1>, |r>} basis, n_shots
@@ -210,7 +212,8 @@ ttn_status ttn_sample(ttn_ctx* ctx, const double* uniforms, int n_shots, int* ou
  * also varies through the gauge and the projectors).
  *   target : same lattice and bond dimension, centre at its root;
  *   F, grad: host, 1 and n_params doubles.
- * The context's state and time are restored on return.  No decay (gamma must
+ * The context's state and time are restored on success (after an error they
+ * are undefined: reload or reset the state).  No decay (gamma must
  * be 0), n_steps >= 1, dt > 0, rows inside the schedule, fields 0 or 1,
  * 1 <= n_quad <= 8, else TTN_ERR_ARG. */
 ttn_status ttn_fidelity_gradient(ttn_ctx* ctx, const ttn_ctx* target, double dt, int n_steps, int n_params,
